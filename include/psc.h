@@ -1,0 +1,224 @@
+/*
+ * psc.h -- C ABI of the GB300 voxel hop engine (pSpatiocyte's diffusion and
+ * collision step on a hexagonal close-packed lattice).
+ *
+ * Paper: A. Miyauchi, K. Iwamoto, S. N. V. Arjunan, K. Takahashi,
+ * "pSpatiocyte: A Parallel Stochastic Method for Particle Reaction-Diffusion
+ * Systems", arXiv:1605.03726.
+ *
+ * Model (what the calls compute)
+ *   Lattice     ni x nj x nk voxels of radius r_v on an HCP lattice in twisted
+ *               Cartesian coordinates (Sec. 2.1): i is the straight axis, j and
+ *               k zigzag; voxel (i, j, k) has 12 neighbours at distance 2 r_v,
+ *               chosen by the parity of j + k and of k.  Voxel index
+ *               v = i + ni * (j + nj * k).  Each axis is periodic or closed by
+ *               a reflective wall (a hop through a wall fails, Sec. 2.3).
+ *   Species     diffusion coefficient D; hop interval tau = 2 r_v^2 / (3 D)
+ *               (Sec. 2.3, Eq. 3).  D = 0 marks an immobile species.
+ *   Event       the scheduler (Sec. 2.2) picks the mobile species with the
+ *               earliest next diffusion time (events_done + 1) * tau; ties go to
+ *               the lower species index.  In that event every molecule of the
+ *               species draws one of its 12 neighbours and moves there if it is
+ *               vacant (Sec. 2.3); if the neighbour holds a registered
+ *               second-order partner the pair reacts with probability
+ *               p_AB = k / (6 sqrt(2) (D_A + D_B) r_v) (Sec. 2.4.2, Eq. 6,
+ *               clamped to 1).  A species with first-order reactions first
+ *               tests, per molecule, whether one fires (probability
+ *               1 - exp(-sum(k) tau), choice by Eq. 5, Sec. 2.4.1); a molecule
+ *               that fires does not hop in that event.
+ *   Conflicts   all molecules of the due species decide against the grid as
+ *               it was when the event began; a voxel wanted by several goes to
+ *               the lowest molecule id; a voxel left in the event is free only
+ *               from the next event on.  (The paper updates one molecule at a
+ *               time, Sec. 2.3, and says the order barely matters; this
+ *               deterministic synchronous form is what runs in parallel.)
+ *   Products    second order: the first product takes the partner's voxel and
+ *               id, the second the mover's voxel and id.  First order: the
+ *               first product keeps the reactant's voxel and id; a second
+ *               product goes to a uniformly chosen neighbour that was vacant
+ *               at the start of the event (Sec. 2.4.1), contested like a hop,
+ *               and gets a fresh id; fresh ids within one event go to the
+ *               parents in ascending parent id.
+ *   Randomness  Philox4x32-10 keyed by the 64-bit seed; counter
+ *               (molecule id, event index, species << 4, 0) for the event
+ *               draws and (voxel, 0, 1, 0) for placement.  Results are a pure
+ *               function of the model and the seed.
+ *
+ * Ownership and threading
+ *   A psc_lattice is opaque and owns all its device memory; the caller owns
+ *   every host buffer passed in.  Device memory comes from cudaMalloc unless
+ *   psc_set_allocator installed another allocator.  All device work of a
+ *   lattice is queued on its CUDA stream; psc_run and psc_run_events return
+ *   once the work is queued, and device-side errors surface at the next call
+ *   that synchronises (psc_synchronize and every read-out).  One host thread
+ *   at a time per lattice; different lattices are independent.
+ *
+ * Status codes
+ *   0 success; negative values are errors (psc_status_string names them);
+ *   PSC_W_PCLAMP (positive) is a warning: some p_AB exceeded 1 and was clamped.
+ */
+#ifndef PSC_H
+#define PSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSC_OK               0
+#define PSC_E_ARG           -1   /* bad argument (null pointer, bad index, NaN) */
+#define PSC_E_DIMS          -2   /* lattice shape not allowed, see create      */
+#define PSC_E_ORDER         -3   /* call out of order (e.g. add after populate) */
+#define PSC_E_FULL          -4   /* more molecules than voxels                 */
+#define PSC_E_UNSUPPORTED   -5   /* model feature outside this engine          */
+#define PSC_E_NOMEM         -6   /* device or host allocation failed           */
+#define PSC_E_CUDA          -7   /* CUDA runtime error                         */
+#define PSC_E_TIMEOUT       -8   /* a bounded device wait gave up              */
+#define PSC_E_LIMIT         -9   /* event counter (2^32 - 1 events) exhausted  */
+#define PSC_E_CAPACITY     -10   /* a device list overflowed its capacity      */
+#define PSC_W_PCLAMP         1   /* p_AB > 1 clamped to 1 (warning)            */
+
+#define PSC_PERIODIC_I  1u       /* boundary flag bits: set = periodic axis,   */
+#define PSC_PERIODIC_J  2u       /* clear = reflective wall                    */
+#define PSC_PERIODIC_K  4u
+#define PSC_PERIODIC_ALL 7u
+
+#define PSC_MAX_SPECIES    32
+#define PSC_MAX_REACTIONS 128
+
+typedef struct psc_lattice psc_lattice;
+
+/* Counters accumulated on the device when statistics are switched on
+   (psc_options.collect_stats); attempts counts every molecule processed in an
+   event whatever the outcome. */
+typedef struct {
+    uint64_t attempts, hops, collisions, accepted, reactions2, fires, reactions1, births;
+    uint64_t events;          /* species events queued                         */
+    uint64_t launches;        /* kernels launched by this lattice (host count) */
+} psc_stats;
+
+/* Tunables; zero in a field keeps the current value. */
+typedef struct {
+    int32_t resort_period;    /* events of a species between Morton re-sorts of
+                                 its molecule list (default 64; <0 = never)     */
+    int32_t block_threads;    /* threads per block of the event kernels (256)   */
+    int32_t blocks_per_sm;    /* resident blocks per SM for grid sizing (8)     */
+    int32_t collect_stats;    /* 1 = count attempts/hops/... (default 0), -1 off */
+    int32_t graph_events;     /* >0: replay runs of this many single-species
+                                 events from a captured CUDA graph (default 0) */
+} psc_options;
+
+/*
+ * Create an empty lattice (Sec. 2.1).
+ *   ni, nj, nk       extents; a periodic i axis needs ni >= 3, a periodic j
+ *                    (k) axis needs an even nj (nk) >= 4 so that the parity
+ *                    stencil wraps consistently; ni * nj * nk < 2^31.
+ *   voxel_radius_m   r_v in metres (> 0).
+ *   boundary_flags   PSC_PERIODIC_* bits.
+ *   device           CUDA device ordinal.
+ *   cuda_stream      cudaStream_t to queue work on, or NULL for a stream the
+ *                    library creates and owns.
+ * Errors: PSC_E_ARG, PSC_E_DIMS, PSC_E_CUDA.
+ */
+int psc_lattice_create(psc_lattice **out, int32_t ni, int32_t nj, int32_t nk,
+                       double voxel_radius_m, uint32_t boundary_flags,
+                       int device, void *cuda_stream);
+
+/* Add a species with diffusion coefficient D (m^2/s, >= 0) and initial count
+   (Sec. 2.3).  Before psc_populate only.  Errors: E_ARG, E_ORDER,
+   E_UNSUPPORTED (more than PSC_MAX_SPECIES). */
+int psc_add_species(psc_lattice *L, double D_m2_s, int64_t initial_count,
+                    int32_t *species_out);
+
+/* Register a reaction (Sec. 2.4).  n_reactants = 1: first order, k in 1/s,
+   reactant must be mobile; n_reactants = 2: second order, k in m^3/s, two
+   different species, one reaction per pair.  0..2 products.  Before populate.
+   Errors: E_ARG, E_ORDER, E_UNSUPPORTED (A + A, > 2 products, first order on
+   an immobile species, a pair registered twice, more than 8 first-order
+   reactions of one species, more than PSC_MAX_REACTIONS). */
+int psc_add_reaction(psc_lattice *L, const int32_t *reactants, int32_t n_reactants,
+                     const int32_t *products, int32_t n_products, double k,
+                     int32_t *reaction_out);
+
+/* Freeze the model, allocate device state and place the molecules uniformly
+   at random without replacement (Sec. 3.4 "distributed homogeneously"):
+   every voxel gets the key Philox(seed; v, 0, 1, 0) word 0, voxels sorted by
+   (key, v) are dealt to the species in index order, ids 0, 1, ... in that
+   order.  Synchronous.  Returns PSC_W_PCLAMP if some p_AB > 1 was clamped.
+   Errors: E_ARG, E_ORDER (twice), E_FULL, E_NOMEM, E_CUDA. */
+int psc_populate(psc_lattice *L, uint64_t seed);
+
+/* Queue every event with time <= t_end (Sec. 2.2); the lattice clock becomes
+   max(clock, t_end).  Resumable: run(t1); run(t2) equals run(t2).
+   Asynchronous.  Errors: E_ARG (t_end not finite), E_ORDER, E_LIMIT, E_CUDA. */
+int psc_run(psc_lattice *L, double t_end);
+
+/* Queue the next n_events events regardless of time (clock = time of the last
+   one).  Asynchronous.  Errors as psc_run. */
+int psc_run_events(psc_lattice *L, int64_t n_events);
+
+/* Wait for queued work; reports device-side errors (E_CAPACITY, E_TIMEOUT)
+   and CUDA errors. */
+int psc_synchronize(psc_lattice *L);
+
+/* Molecule counts per species into counts[0 .. n_species-1] (caller-owned,
+   n_species >= species added).  Synchronises. */
+int psc_counts(psc_lattice *L, int64_t *counts, int32_t n_species);
+
+/* Positions (i, j, k) of the molecules of one species into ijk[3 * a], sorted
+   by molecule id, ids into ids[a] if not NULL; *n_out = number of molecules.
+   With cap < *n_out nothing is written and E_ARG is returned (call with
+   cap = 0 to size the buffers).  Synchronises. */
+int psc_coords(psc_lattice *L, int32_t species, int32_t *ijk, uint32_t *ids,
+               int64_t cap, int64_t *n_out);
+
+/* Unwrapped positions in the integer basis X = 2I + P, Y = 3J + (K & 1),
+   Z = K, where I = i + wraps_i * ni (J, K likewise, wraps counted in 16 bits)
+   and P = (J + K) & 1; the centre is (X, Y / sqrt 3, 2 sqrt(2/3) Z) r_v, so
+   squared displacements follow exactly (App. C, Eq. 14).  Sorted by id.
+   Synchronises. */
+int psc_unwrapped(psc_lattice *L, int32_t species, int32_t *xyz, uint32_t *ids,
+                  int64_t cap, int64_t *n_out);
+
+/* Copy the occupancy grid (ni*nj*nk uint16: 0 vacant, s + 1 species s) into
+   occ (caller-owned).  Synchronises. */
+int psc_grid(psc_lattice *L, uint16_t *occ);
+
+/* Simulated time (seconds) and number of events queued so far. */
+int psc_time(const psc_lattice *L, double *t);
+int psc_event_index(const psc_lattice *L, uint32_t *g);
+
+/* Device counters (see psc_stats).  Synchronises. */
+int psc_stats_get(psc_lattice *L, psc_stats *s);
+
+/* Change tunables (psc_options); allowed at any time between calls. */
+int psc_set_options(psc_lattice *L, const psc_options *opt);
+
+/* Hop interval of a species and p_AB of a second-order reaction as the engine
+   computes them (Sec. 2.3 Eq. 3, Sec. 2.4.2 Eq. 6; p_AB before clamping). */
+double psc_tau(const psc_lattice *L, int32_t species);
+double psc_p_ab(const psc_lattice *L, int32_t reaction);
+
+/* Bytes of device memory the lattice holds after psc_populate (or would hold,
+   computed from its shape and model, before). */
+int psc_device_bytes(const psc_lattice *L, int64_t *bytes);
+
+/* Free the lattice and its device memory (waits for its queued work). */
+void psc_lattice_destroy(psc_lattice *L);
+
+/* Name of a status code. */
+const char *psc_status_string(int status);
+
+/* Install a device allocator for subsequent allocations (NULL, NULL restores
+   cudaMalloc / cudaFree).  alloc(bytes, device, stream, ctx) returns a device
+   pointer or NULL; release(ptr, device, stream, ctx) frees it.  Process-wide. */
+typedef void *(*psc_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*psc_free_fn)(void *ptr, int device, void *stream, void *ctx);
+int psc_set_allocator(psc_alloc_fn alloc, psc_free_fn release, void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,245 @@
+"""GB300 voxel hop engine: pSpatiocyte's diffusion-and-collision step on an HCP lattice.
+
+Thin ctypes binding over the C ABI declared in include/psc.h (Miyauchi et al.,
+arXiv:1605.03726, Sec. 2.1-2.4).  It only marshals arguments: every step of an
+event runs in the sm_103a kernels of _build/libpsc.so, and importing fails
+loudly if that library cannot be built or loaded -- there is no CPU path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build as _build
+
+OK, E_ARG, E_DIMS, E_ORDER, E_FULL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_LIMIT, E_CAPACITY = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
+W_PCLAMP = 1
+PERIODIC_I, PERIODIC_J, PERIODIC_K, PERIODIC_ALL = 1, 2, 4, 7
+MAX_SPECIES = 32
+
+_lib = None
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "attempts", "hops", "collisions", "accepted", "reactions2", "fires", "reactions1", "births",
+        "events", "launches")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events")]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib():
+    """The loaded libpsc.so (built in-tree on first use if sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build()
+        if not os.path.exists(path):
+            raise ImportError("libpsc.so missing at %s" % path)
+        L = ctypes.CDLL(path)
+        P, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.c_double)
+        sig = {
+            "psc_lattice_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, i32, dbl, u32, ctypes.c_int, P]),
+            "psc_add_species": (ctypes.c_int, [P, dbl, i64, ctypes.POINTER(i32)]),
+            "psc_add_reaction": (ctypes.c_int, [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32, dbl,
+                                                ctypes.POINTER(i32)]),
+            "psc_populate": (ctypes.c_int, [P, u64]),
+            "psc_run": (ctypes.c_int, [P, dbl]),
+            "psc_run_events": (ctypes.c_int, [P, i64]),
+            "psc_synchronize": (ctypes.c_int, [P]),
+            "psc_counts": (ctypes.c_int, [P, P, i32]),
+            "psc_coords": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
+            "psc_unwrapped": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
+            "psc_grid": (ctypes.c_int, [P, P]),
+            "psc_time": (ctypes.c_int, [P, ctypes.POINTER(dbl)]),
+            "psc_event_index": (ctypes.c_int, [P, ctypes.POINTER(u32)]),
+            "psc_stats_get": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
+            "psc_set_options": (ctypes.c_int, [P, ctypes.POINTER(Options)]),
+            "psc_tau": (dbl, [P, i32]),
+            "psc_p_ab": (dbl, [P, i32]),
+            "psc_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
+            "psc_lattice_destroy": (None, [P]),
+            "psc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "psc_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_populate", "psc_run",
+            "psc_run_events", "psc_synchronize", "psc_counts", "psc_coords", "psc_unwrapped", "psc_grid",
+            "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_tau", "psc_p_ab",
+            "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator")
+
+
+class EngineError(RuntimeError):
+    def __init__(self, fn, rc):
+        name = lib().psc_status_string(rc).decode()
+        super().__init__("%s failed: %s (%d)" % (fn, name, rc))
+        self.rc = rc
+
+
+def _check(fn, rc, allow=(OK,)):
+    if rc not in allow:
+        raise EngineError(fn, rc)
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+_torch_hooks = None
+
+
+def use_torch_allocator():
+    """Route the engine's device allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    import torch
+
+    def alloc(nbytes, device, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:
+            return None
+
+    def free(ptr, device, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _torch_hooks = (ALLOC_FN(alloc), FREE_FN(free))
+    _check("psc_set_allocator", lib().psc_set_allocator(_torch_hooks[0], _torch_hooks[1], None))
+
+
+def use_cuda_malloc():
+    global _torch_hooks
+    _check("psc_set_allocator", lib().psc_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _torch_hooks = None
+
+
+class Lattice:
+    """One lattice on one GPU; methods mirror the psc_* entry points."""
+
+    def __init__(self, ni, nj, nk, voxel_radius=10e-9, boundary=PERIODIC_ALL, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        _check("psc_lattice_create", lib().psc_lattice_create(
+            ctypes.byref(self._h), ni, nj, nk, voxel_radius, boundary, device,
+            ctypes.c_void_p(stream) if stream else None))
+        self.shape = (ni, nj, nk)
+        self.n_species = 0
+
+    def close(self):
+        if self._h:
+            lib().psc_lattice_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_species(self, D, count):
+        s = ctypes.c_int32()
+        _check("psc_add_species", lib().psc_add_species(self._h, float(D), int(count), ctypes.byref(s)))
+        self.n_species += 1
+        return s.value
+
+    def add_reaction(self, reactants, products, k):
+        r = (ctypes.c_int32 * max(1, len(reactants)))(*reactants)
+        p = (ctypes.c_int32 * max(1, len(products)))(*products)
+        out = ctypes.c_int32()
+        _check("psc_add_reaction", lib().psc_add_reaction(
+            self._h, r, len(reactants), p, len(products), float(k), ctypes.byref(out)))
+        return out.value
+
+    def populate(self, seed):
+        return _check("psc_populate", lib().psc_populate(self._h, int(seed)), (OK, W_PCLAMP))
+
+    def run(self, t_end):
+        _check("psc_run", lib().psc_run(self._h, float(t_end)))
+
+    def run_events(self, n):
+        _check("psc_run_events", lib().psc_run_events(self._h, int(n)))
+
+    def synchronize(self):
+        _check("psc_synchronize", lib().psc_synchronize(self._h))
+
+    def set_options(self, **kw):
+        o = Options(**kw)
+        _check("psc_set_options", lib().psc_set_options(self._h, ctypes.byref(o)))
+
+    def counts(self):
+        c = np.zeros(max(1, self.n_species), dtype=np.int64)
+        _check("psc_counts", lib().psc_counts(self._h, _ptr(c), max(1, self.n_species)))
+        return c[: self.n_species]
+
+    def coords(self, species):
+        n = ctypes.c_int64()
+        _check("psc_coords", lib().psc_coords(self._h, species, None, None, 0, ctypes.byref(n)), (OK, E_ARG))
+        ijk = np.zeros((max(1, n.value), 3), dtype=np.int32)
+        ids = np.zeros(max(1, n.value), dtype=np.uint32)
+        _check("psc_coords", lib().psc_coords(self._h, species, _ptr(ijk), _ptr(ids), n.value, ctypes.byref(n)))
+        return ijk[: n.value], ids[: n.value]
+
+    def unwrapped(self, species):
+        n = ctypes.c_int64()
+        _check("psc_unwrapped", lib().psc_unwrapped(self._h, species, None, None, 0, ctypes.byref(n)), (OK, E_ARG))
+        xyz = np.zeros((max(1, n.value), 3), dtype=np.int32)
+        ids = np.zeros(max(1, n.value), dtype=np.uint32)
+        _check("psc_unwrapped", lib().psc_unwrapped(self._h, species, _ptr(xyz), _ptr(ids), n.value,
+                                                    ctypes.byref(n)))
+        return xyz[: n.value], ids[: n.value]
+
+    def grid(self):
+        ni, nj, nk = self.shape
+        g = np.zeros(ni * nj * nk, dtype=np.uint16)
+        _check("psc_grid", lib().psc_grid(self._h, _ptr(g)))
+        return g
+
+    def time(self):
+        t = ctypes.c_double()
+        _check("psc_time", lib().psc_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    def event_index(self):
+        g = ctypes.c_uint32()
+        _check("psc_event_index", lib().psc_event_index(self._h, ctypes.byref(g)))
+        return g.value
+
+    def stats(self):
+        s = Stats()
+        _check("psc_stats_get", lib().psc_stats_get(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def tau(self, species):
+        return lib().psc_tau(self._h, species)
+
+    def p_ab(self, reaction):
+        return lib().psc_p_ab(self._h, reaction)
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        _check("psc_device_bytes", lib().psc_device_bytes(self._h, ctypes.byref(b)))
+        return b.value

@@ -1,0 +1,781 @@
+// psc_api.cpp -- host runtime of the hop engine: the C ABI of include/psc.h.
+//
+// The host owns the model (species, reactions), derives the per-species
+// constants of the paper (hop interval, Sec. 2.3; acceptance p_AB,
+// Sec. 2.4.2; first-order firing, Sec. 2.4.1), runs the event scheduler
+// (Sec. 2.2) and queues the kernels of each event on the lattice's stream.
+// No step of an event runs on the host: the kernels read the molecule counts
+// from device memory, so the host never waits for the device between events.
+#include "psc.h"
+#include "psc_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+using namespace psc;
+
+namespace {
+
+psc_alloc_fn g_alloc = nullptr;
+psc_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+std::mutex g_alloc_mu;
+
+struct Species {
+    double D = 0.0;
+    int64_t n0 = 0;
+    double tau = 0.0;
+    uint64_t done = 0;
+    int n_fo = 0;
+    int fo[kMaxFirstOrder] = {};
+};
+
+struct Reaction {
+    int nr = 0, np = 0;
+    int r[2] = {0, 0}, p[2] = {0, 0};
+    double k = 0.0;
+    double prob = 0.0;
+};
+
+// floor(min(p, 1) * 2^32): a 32-bit uniform u passes with probability p iff u < T
+uint64_t prob_threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1ull << 32;
+    return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+// Sec. 2.3, Eq. 3: mean time to hop one voxel diameter, tau_d = 2 r_v^2 / (3 D)
+double hop_interval(double rv, double D) { return (2.0 * rv * rv) / (3.0 * D); }
+
+// Sec. 2.4.2, Eq. 6: discrete Collins-Kimball acceptance of a collision
+double acceptance(double k, double DA, double DB, double rv)
+{
+    return k / (6.0 * std::sqrt(2.0) * (DA + DB) * rv);
+}
+
+}  // namespace
+
+struct psc_lattice {
+    int32_t ni = 0, nj = 0, nk = 0;
+    int64_t V = 0;
+    double rv = 0.0;
+    uint32_t bflags = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+
+    int nsp = 0;
+    Species sp[kMaxSpecies];
+    int nrx = 0;
+    Reaction rx[kMaxReactions];
+    int8_t pair[kMaxSpecies][kMaxSpecies];
+
+    bool populated = false;
+    bool clamped = false;
+    uint64_t seed = 0;
+    uint32_t g = 0;
+    double clock = 0.0;
+
+    Geometry geo{};
+    ModelDev model_h{};
+    ModelDev* model_d = nullptr;
+    uint16_t* occ = nullptr;
+    uint32_t* claim = nullptr;
+    Scalars* sc = nullptr;
+    Birth* births = nullptr;
+    int32_t births_cap = 0;
+    SpeciesList tmp{};
+    int32_t cap[kMaxSpecies] = {};
+    uint32_t* rs_keys = nullptr;      // re-sort keys / values
+    uint32_t* rs_vals = nullptr;
+    SortScratch rs_scratch;
+    int64_t rs_max = 0;
+
+    bool general[kMaxSpecies] = {};
+    bool fo2[kMaxSpecies] = {};
+    std::vector<int> reconcile[kMaxSpecies];
+    uint64_t since_resort[kMaxSpecies] = {};
+
+    psc_options opt{64, 256, 8, 0, 0};
+    int64_t launches = 0;
+    uint64_t events = 0;
+    int sticky = PSC_OK;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int cuda_fail(psc_lattice* L, cudaError_t e)
+{
+    if (e == cudaSuccess) return PSC_OK;
+    if (L) L->sticky = (e == cudaErrorMemoryAllocation) ? PSC_E_NOMEM : PSC_E_CUDA;
+    return e == cudaErrorMemoryAllocation ? PSC_E_NOMEM : PSC_E_CUDA;
+}
+
+void* dev_alloc(psc_lattice* L, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        if (g_alloc) p = g_alloc(bytes, L->device, L->stream, g_alloc_ctx);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    }
+    if (p) L->allocs.push_back(p);
+    return p;
+}
+
+void dev_free_all(psc_lattice* L)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    for (void* p : L->allocs) {
+        if (g_free) g_free(p, L->device, L->stream, g_alloc_ctx);
+        else cudaFree(p);
+    }
+    L->allocs.clear();
+}
+
+void dev_free_one(psc_lattice* L, void* p)
+{
+    auto it = std::find(L->allocs.begin(), L->allocs.end(), p);
+    if (it == L->allocs.end()) return;
+    L->allocs.erase(it);
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_free) g_free(p, L->device, L->stream, g_alloc_ctx);
+    else cudaFree(p);
+}
+
+int event_blocks(const psc_lattice* L, int64_t work)
+{
+    const int64_t want = (work + L->opt.block_threads - 1) / L->opt.block_threads;
+    const int64_t cap = (int64_t)L->sm_count * L->opt.blocks_per_sm;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+// set-up of one event of species s, everything passed by value
+EventArgs event_args(const psc_lattice* L, int s)
+{
+    EventArgs a{};
+    a.geo = L->geo;
+    a.occ = L->occ;
+    a.claim = L->claim;
+    a.list = L->model_h.lists[s];
+    a.count = &L->sc->counts[s];
+    a.model = L->model_d;
+    a.sc = L->sc;
+    a.births = L->births;
+    a.births_cap = L->births_cap;
+    a.key0 = (uint32_t)L->seed;
+    a.key1 = (uint32_t)(L->seed >> 32);
+    a.g = L->g;
+    a.s = s;
+    a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
+    return a;
+}
+
+int resort(psc_lattice* L, int s)
+{
+    const int blocks = event_blocks(L, L->cap[s]);
+    const SpeciesList& list = L->model_h.lists[s];
+    const int32_t* count = &L->sc->counts[s];
+    launch_morton_keys(list, count, L->geo, L->rs_keys, L->rs_vals, blocks, L->stream);
+    if (radix_sort_pairs(L->rs_keys, L->rs_vals, count, 0, L->cap[s], 30, L->rs_scratch, L->stream,
+                         &L->launches) != 0)
+        return cuda_fail(L, cudaErrorUnknown);
+    launch_permute(list, L->tmp, L->rs_vals, count, blocks, L->stream);
+    launch_copy_list(L->tmp, list, count, blocks, L->stream);
+    L->launches += 3;
+    return PSC_OK;
+}
+
+int enqueue_event(psc_lattice* L, int s)
+{
+    const EventArgs a = event_args(L, s);
+    const int threads = L->opt.block_threads;
+    const int blocks = event_blocks(L, L->cap[s]);
+    launch_claim(a, L->general[s], blocks, threads, L->stream);
+    launch_commit(a, L->general[s], blocks, threads, L->stream);
+    L->launches += 2;
+    for (int x : L->reconcile[s]) {
+        ReconcileArgs r{};
+        r.occ = L->occ;
+        r.x = x;
+        r.list = L->model_h.lists[x];
+        r.tmp = L->tmp;
+        r.model = L->model_d;
+        r.sc = L->sc;
+        const int rb = event_blocks(L, L->cap[x]);
+        launch_reconcile(r, rb, threads, L->stream);
+        launch_copyback(r, rb, threads, L->stream);
+        L->launches += 2;
+    }
+    if (L->fo2[s]) {
+        launch_births(a, L->stream);
+        L->launches += 1;
+    }
+    L->events++;
+    if (L->opt.resort_period > 0 && ++L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
+        L->since_resort[s] = 0;
+        int rc = resort(L, s);
+        if (rc) return rc;
+    }
+    return cuda_fail(L, cudaPeekAtLastError());
+}
+
+// Sec. 2.2: the next event belongs to the mobile species whose next diffusion
+// time (events done + 1) * tau is earliest; ties go to the lower index.
+bool next_event(const psc_lattice* L, int* s_out, double* t_out)
+{
+    int best = -1;
+    double tb = 0.0;
+    for (int s = 0; s < L->nsp; ++s) {
+        if (!(L->sp[s].D > 0.0)) continue;
+        const double t = (double)(L->sp[s].done + 1) * L->sp[s].tau;
+        if (best < 0 || t < tb) { best = s; tb = t; }
+    }
+    *s_out = best;
+    *t_out = tb;
+    return best >= 0;
+}
+
+int check_device(psc_lattice* L)
+{
+    cudaError_t e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) return cuda_fail(L, e);
+    if (!L->populated) return L->sticky;
+    int32_t err = 0;
+    e = cudaMemcpy(&err, &L->sc->err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(L, e);
+    if (err) L->sticky = PSC_E_CAPACITY;
+    return L->sticky;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~DevGuard() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* psc_status_string(int s)
+{
+    switch (s) {
+    case PSC_OK: return "PSC_OK";
+    case PSC_E_ARG: return "PSC_E_ARG";
+    case PSC_E_DIMS: return "PSC_E_DIMS";
+    case PSC_E_ORDER: return "PSC_E_ORDER";
+    case PSC_E_FULL: return "PSC_E_FULL";
+    case PSC_E_UNSUPPORTED: return "PSC_E_UNSUPPORTED";
+    case PSC_E_NOMEM: return "PSC_E_NOMEM";
+    case PSC_E_CUDA: return "PSC_E_CUDA";
+    case PSC_E_TIMEOUT: return "PSC_E_TIMEOUT";
+    case PSC_E_LIMIT: return "PSC_E_LIMIT";
+    case PSC_E_CAPACITY: return "PSC_E_CAPACITY";
+    case PSC_W_PCLAMP: return "PSC_W_PCLAMP";
+    default: return "PSC_UNKNOWN";
+    }
+}
+
+int psc_set_allocator(psc_alloc_fn alloc, psc_free_fn release, void* ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return PSC_E_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return PSC_OK;
+}
+
+int psc_lattice_create(psc_lattice** out, int32_t ni, int32_t nj, int32_t nk, double rv,
+                       uint32_t bflags, int device, void* cuda_stream)
+{
+    if (!out) return PSC_E_ARG;
+    *out = nullptr;
+    if (!(rv > 0.0) || !std::isfinite(rv) || bflags > 7u || device < 0) return PSC_E_ARG;
+    if (ni < 1 || nj < 1 || nk < 1) return PSC_E_DIMS;
+    const int64_t V = (int64_t)ni * nj * nk;
+    if (V >= (1ll << 31)) return PSC_E_DIMS;
+    if ((bflags & PSC_PERIODIC_I) && ni < 3) return PSC_E_DIMS;
+    if ((bflags & PSC_PERIODIC_J) && (nj < 4 || (nj & 1))) return PSC_E_DIMS;
+    if ((bflags & PSC_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSC_E_DIMS;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) return PSC_E_CUDA;
+    psc_lattice* L = new (std::nothrow) psc_lattice();
+    if (!L) return PSC_E_NOMEM;
+    L->ni = ni; L->nj = nj; L->nk = nk; L->V = V; L->rv = rv; L->bflags = bflags; L->device = device;
+    std::memset(L->pair, -1, sizeof(L->pair));
+    DevGuard dg(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete L; return PSC_E_CUDA; }
+    L->sm_count = prop.multiProcessorCount;
+    if (cuda_stream) {
+        L->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) { delete L; return PSC_E_CUDA; }
+        L->own_stream = true;
+    }
+    L->geo.ni = ni; L->geo.nj = nj; L->geo.nk = nk; L->geo.bflags = bflags;
+    L->geo.ninj = (uint32_t)ni * (uint32_t)nj;
+    L->geo.div_ni = make_fastdiv((uint32_t)ni);
+    L->geo.div_ninj = make_fastdiv(L->geo.ninj);
+    *out = L;
+    return PSC_OK;
+}
+
+int psc_add_species(psc_lattice* L, double D, int64_t n0, int32_t* species_out)
+{
+    if (!L) return PSC_E_ARG;
+    if (L->populated) return PSC_E_ORDER;
+    if (!(D >= 0.0) || !std::isfinite(D) || n0 < 0) return PSC_E_ARG;
+    if (L->nsp >= kMaxSpecies) return PSC_E_UNSUPPORTED;
+    Species& S = L->sp[L->nsp];
+    S = Species();
+    S.D = D;
+    S.n0 = n0;
+    S.tau = D > 0.0 ? hop_interval(L->rv, D) : 0.0;
+    if (species_out) *species_out = L->nsp;
+    L->nsp++;
+    return PSC_OK;
+}
+
+int psc_add_reaction(psc_lattice* L, const int32_t* re, int32_t nr, const int32_t* pr, int32_t np,
+                     double k, int32_t* rx_out)
+{
+    if (!L) return PSC_E_ARG;
+    if (L->populated) return PSC_E_ORDER;
+    if (nr < 1 || nr > 2 || np < 0 || !re || (np > 0 && !pr)) return PSC_E_ARG;
+    if (!(k >= 0.0) || !std::isfinite(k)) return PSC_E_ARG;
+    if (np > 2) return PSC_E_UNSUPPORTED;
+    for (int a = 0; a < nr; ++a) if (re[a] < 0 || re[a] >= L->nsp) return PSC_E_ARG;
+    for (int a = 0; a < np; ++a) if (pr[a] < 0 || pr[a] >= L->nsp) return PSC_E_ARG;
+    if (L->nrx >= kMaxReactions) return PSC_E_UNSUPPORTED;
+    if (nr == 2) {
+        if (re[0] == re[1]) return PSC_E_UNSUPPORTED;
+        if (!(L->sp[re[0]].D + L->sp[re[1]].D > 0.0)) return PSC_E_UNSUPPORTED;
+        if (L->pair[re[0]][re[1]] >= 0) return PSC_E_UNSUPPORTED;
+    } else {
+        if (!(L->sp[re[0]].D > 0.0)) return PSC_E_UNSUPPORTED;
+        if (L->sp[re[0]].n_fo >= kMaxFirstOrder) return PSC_E_UNSUPPORTED;
+    }
+    Reaction& R = L->rx[L->nrx];
+    R = Reaction();
+    R.nr = nr; R.np = np; R.k = k;
+    for (int a = 0; a < nr; ++a) R.r[a] = re[a];
+    for (int a = 0; a < np; ++a) R.p[a] = pr[a];
+    if (nr == 2) {
+        L->pair[re[0]][re[1]] = (int8_t)L->nrx;
+        L->pair[re[1]][re[0]] = (int8_t)L->nrx;
+    } else {
+        Species& S = L->sp[re[0]];
+        S.fo[S.n_fo++] = L->nrx;
+    }
+    if (rx_out) *rx_out = L->nrx;
+    L->nrx++;
+    return PSC_OK;
+}
+
+double psc_tau(const psc_lattice* L, int32_t s)
+{
+    if (!L || s < 0 || s >= L->nsp || !(L->sp[s].D > 0.0)) return 0.0;
+    return L->sp[s].tau;
+}
+
+double psc_p_ab(const psc_lattice* L, int32_t r)
+{
+    if (!L || r < 0 || r >= L->nrx || L->rx[r].nr != 2) return 0.0;
+    const Reaction& R = L->rx[r];
+    return acceptance(R.k, L->sp[R.r[0]].D, L->sp[R.r[1]].D, L->rv);
+}
+
+int psc_populate(psc_lattice* L, uint64_t seed)
+{
+    if (!L) return PSC_E_ARG;
+    if (L->populated) return PSC_E_ORDER;
+    int64_t N = 0;
+    for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
+    if (N > L->V) return PSC_E_FULL;
+    DevGuard dg(L->device);
+    L->seed = seed;
+
+    // ---- frozen constants (Sec. 2.3, 2.4.1, 2.4.2) ----
+    ModelDev& M = L->model_h;
+    std::memset(&M, 0, sizeof(M));
+    std::memcpy(M.pair, L->pair, sizeof(M.pair));
+    bool growth = false;
+    bool is_product[kMaxSpecies] = {};
+    for (int r = 0; r < L->nrx; ++r) {
+        Reaction& R = L->rx[r];
+        ReactionDev& D = M.rx[r];
+        D.np = R.np;
+        D.p0 = R.np > 0 ? R.p[0] : 0;
+        D.p1 = R.np > 1 ? R.p[1] : 0;
+        for (int a = 0; a < R.np; ++a) is_product[R.p[a]] = true;
+        if (R.nr == 2) {
+            R.prob = acceptance(R.k, L->sp[R.r[0]].D, L->sp[R.r[1]].D, L->rv);
+            if (R.prob > 1.0) L->clamped = true;
+            D.T = prob_threshold(R.prob);
+        } else if (R.np == 2) {
+            growth = true;
+        }
+    }
+    for (int s = 0; s < L->nsp; ++s) {
+        const Species& S = L->sp[s];
+        M.n_fo[s] = S.n_fo;
+        if (S.n_fo == 0) continue;
+        // per molecule and per own diffusion event: fire with 1 - exp(-a0 tau)
+        double ktot = 0.0;
+        for (int u = 0; u < S.n_fo; ++u) ktot += L->rx[S.fo[u]].k;
+        M.T_fire[s] = prob_threshold(-std::expm1(-ktot * S.tau));
+        // Eq. 5: reaction u is the first whose cumulative share reaches a0 R
+        double cum = 0.0;
+        for (int u = 0; u < S.n_fo; ++u) {
+            cum += L->rx[S.fo[u]].k;
+            M.fo_rx[s][u] = S.fo[u];
+            M.fo_cum[s][u] = (u == S.n_fo - 1) ? (1ull << 32)
+                                               : prob_threshold(ktot > 0.0 ? cum / ktot : 1.0);
+        }
+    }
+    // ---- which lists an event can touch ----
+    for (int s = 0; s < L->nsp; ++s) {
+        bool so = false;
+        L->reconcile[s].clear();
+        for (int r = 0; r < L->nsp; ++r) if (L->pair[s][r] >= 0) so = true;
+        L->general[s] = so || L->sp[s].n_fo > 0;
+        L->fo2[s] = false;
+        for (int u = 0; u < L->sp[s].n_fo; ++u)
+            if (L->rx[L->sp[s].fo[u]].np == 2) L->fo2[s] = true;
+        if (L->general[s]) {
+            L->reconcile[s].push_back(s);
+            for (int r = 0; r < L->nsp; ++r) if (L->pair[s][r] >= 0) L->reconcile[s].push_back(r);
+        }
+    }
+    // ---- capacities: a list only grows if its species is a product ----
+    const int64_t total_bound = growth ? L->V : N;
+    int64_t max_cap = 1, max_mobile = 1;
+    for (int s = 0; s < L->nsp; ++s) {
+        int64_t c = is_product[s] ? std::min<int64_t>(L->V, std::max<int64_t>(total_bound, L->sp[s].n0))
+                                  : L->sp[s].n0;
+        c = std::max<int64_t>(c, 1);
+        L->cap[s] = (int32_t)c;
+        max_cap = std::max(max_cap, c);
+        if (L->sp[s].D > 0.0) max_mobile = std::max(max_mobile, c);
+    }
+    bool any_fo2 = false;
+    for (int s = 0; s < L->nsp; ++s) any_fo2 = any_fo2 || L->fo2[s];
+
+    // ---- device memory ----
+    const size_t V = (size_t)L->V;
+    L->occ = (uint16_t*)dev_alloc(L, V * sizeof(uint16_t));
+    L->claim = (uint32_t*)dev_alloc(L, V * sizeof(uint32_t));
+    L->sc = (Scalars*)dev_alloc(L, sizeof(Scalars));
+    L->model_d = (ModelDev*)dev_alloc(L, sizeof(ModelDev));
+    if (!L->occ || !L->claim || !L->sc || !L->model_d) return PSC_E_NOMEM;
+    for (int s = 0; s < L->nsp; ++s) {
+        SpeciesList& l = M.lists[s];
+        l.cap = L->cap[s];
+        l.vox = (int32_t*)dev_alloc(L, (size_t)l.cap * 4);
+        l.ids = (uint32_t*)dev_alloc(L, (size_t)l.cap * 4);
+        l.img = (uint64_t*)dev_alloc(L, (size_t)l.cap * 8);
+        if (!l.vox || !l.ids || !l.img) return PSC_E_NOMEM;
+    }
+    L->tmp.cap = (int32_t)max_cap;
+    L->tmp.vox = (int32_t*)dev_alloc(L, (size_t)max_cap * 4);
+    L->tmp.ids = (uint32_t*)dev_alloc(L, (size_t)max_cap * 4);
+    L->tmp.img = (uint64_t*)dev_alloc(L, (size_t)max_cap * 8);
+    if (!L->tmp.vox || !L->tmp.ids || !L->tmp.img) return PSC_E_NOMEM;
+    L->births_cap = any_fo2 ? 8192 : 1;
+    L->births = (Birth*)dev_alloc(L, (size_t)L->births_cap * sizeof(Birth));
+    L->rs_max = max_mobile;
+    L->rs_keys = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+    L->rs_vals = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+    void* rs = dev_alloc(L, sort_scratch_bytes(max_mobile));
+    if (!L->births || !L->rs_keys || !L->rs_vals || !rs) return PSC_E_NOMEM;
+    sort_scratch_bind(L->rs_scratch, rs, max_mobile);
+
+    cudaStream_t st = L->stream;
+    upload_stencil(st);
+    int rc = cuda_fail(L, cudaMemcpyAsync(L->model_d, &M, sizeof(M), cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    Scalars sh;
+    std::memset(&sh, 0, sizeof(sh));
+    for (int s = 0; s < L->nsp; ++s) sh.counts[s] = (int32_t)L->sp[s].n0;
+    sh.next_id = (uint32_t)N;
+    if ((rc = cuda_fail(L, cudaMemcpyAsync(L->sc, &sh, sizeof(sh), cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->occ, 0, V * sizeof(uint16_t), st)))) return rc;
+    const int fill_blocks = L->sm_count * 8;
+    launch_fill_u32(L->claim, kNoClaim, V, fill_blocks, st);
+
+    // ---- placement: voxels sorted by (Philox key, voxel) dealt to the species ----
+    if (N > 0) {
+        uint32_t* keys = (uint32_t*)dev_alloc(L, V * 4);
+        uint32_t* vals = (uint32_t*)dev_alloc(L, V * 4);
+        void* scratch = dev_alloc(L, sort_scratch_bytes(L->V));
+        if (!keys || !vals || !scratch) return PSC_E_NOMEM;
+        SortScratch ss;
+        sort_scratch_bind(ss, scratch, L->V);
+        launch_populate_keys(keys, vals, (uint32_t)V, (uint32_t)seed, (uint32_t)(seed >> 32), fill_blocks, st);
+        if (radix_sort_pairs(keys, vals, nullptr, L->V, L->V, 32, ss, st, &L->launches) != 0)
+            return cuda_fail(L, cudaErrorUnknown);
+        int64_t off[kMaxSpecies + 1];
+        off[0] = 0;
+        for (int s = 0; s < L->nsp; ++s) off[s + 1] = off[s] + L->sp[s].n0;
+        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->model_d, fill_blocks, st);
+        if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
+        dev_free_one(L, keys);
+        dev_free_one(L, vals);
+        dev_free_one(L, scratch);
+    }
+    if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
+    L->g = 0;
+    L->clock = 0.0;
+    L->populated = true;
+    return L->clamped ? PSC_W_PCLAMP : PSC_OK;
+}
+
+int psc_run(psc_lattice* L, double t_end)
+{
+    if (!L || !std::isfinite(t_end)) return PSC_E_ARG;
+    if (!L->populated) return PSC_E_ORDER;
+    if (L->sticky) return L->sticky;
+    DevGuard dg(L->device);
+    for (;;) {
+        int s;
+        double t;
+        if (!next_event(L, &s, &t) || t > t_end) break;
+        if (L->g == UINT32_MAX) return PSC_E_LIMIT;
+        int rc = enqueue_event(L, s);
+        if (rc) return rc;
+        L->sp[s].done++;
+        L->g++;
+        L->clock = t;
+    }
+    if (t_end > L->clock) L->clock = t_end;
+    return PSC_OK;
+}
+
+int psc_run_events(psc_lattice* L, int64_t n_events)
+{
+    if (!L || n_events < 0) return PSC_E_ARG;
+    if (!L->populated) return PSC_E_ORDER;
+    if (L->sticky) return L->sticky;
+    DevGuard dg(L->device);
+    for (int64_t e = 0; e < n_events; ++e) {
+        int s;
+        double t;
+        if (!next_event(L, &s, &t)) break;
+        if (L->g == UINT32_MAX) return PSC_E_LIMIT;
+        int rc = enqueue_event(L, s);
+        if (rc) return rc;
+        L->sp[s].done++;
+        L->g++;
+        L->clock = t;
+    }
+    return PSC_OK;
+}
+
+int psc_synchronize(psc_lattice* L)
+{
+    if (!L) return PSC_E_ARG;
+    DevGuard dg(L->device);
+    return check_device(L);
+}
+
+int psc_counts(psc_lattice* L, int64_t* counts, int32_t n)
+{
+    if (!L || !counts || n < L->nsp) return PSC_E_ARG;
+    for (int s = 0; s < n; ++s) counts[s] = s < L->nsp ? L->sp[s].n0 : 0;
+    if (!L->populated) return PSC_OK;
+    DevGuard dg(L->device);
+    int rc = check_device(L);
+    if (rc) return rc;
+    int32_t c[kMaxSpecies];
+    if ((rc = cuda_fail(L, cudaMemcpy(c, L->sc->counts, sizeof(c), cudaMemcpyDeviceToHost)))) return rc;
+    for (int s = 0; s < L->nsp; ++s) counts[s] = c[s];
+    return PSC_OK;
+}
+
+static int read_list(psc_lattice* L, int32_t s, std::vector<int32_t>& vox, std::vector<uint32_t>& ids,
+                     std::vector<uint64_t>* img)
+{
+    int rc = check_device(L);
+    if (rc) return rc;
+    int32_t n = 0;
+    if ((rc = cuda_fail(L, cudaMemcpy(&n, &L->sc->counts[s], 4, cudaMemcpyDeviceToHost)))) return rc;
+    const SpeciesList& l = L->model_h.lists[s];
+    vox.resize(n);
+    ids.resize(n);
+    if (n > 0) {
+        if ((rc = cuda_fail(L, cudaMemcpy(vox.data(), l.vox, (size_t)n * 4, cudaMemcpyDeviceToHost)))) return rc;
+        if ((rc = cuda_fail(L, cudaMemcpy(ids.data(), l.ids, (size_t)n * 4, cudaMemcpyDeviceToHost)))) return rc;
+        if (img) {
+            img->resize(n);
+            if ((rc = cuda_fail(L, cudaMemcpy(img->data(), l.img, (size_t)n * 8, cudaMemcpyDeviceToHost)))) return rc;
+        }
+    }
+    return PSC_OK;
+}
+
+int psc_coords(psc_lattice* L, int32_t s, int32_t* ijk, uint32_t* ids_out, int64_t cap, int64_t* n_out)
+{
+    if (!L || !n_out || s < 0 || s >= L->nsp) return PSC_E_ARG;
+    if (!L->populated) return PSC_E_ORDER;
+    DevGuard dg(L->device);
+    std::vector<int32_t> vox;
+    std::vector<uint32_t> ids;
+    int rc = read_list(L, s, vox, ids, nullptr);
+    if (rc) return rc;
+    const int64_t n = (int64_t)vox.size();
+    *n_out = n;
+    if (n > cap || (n > 0 && !ijk)) return PSC_E_ARG;
+    std::vector<int64_t> order(n);
+    for (int64_t a = 0; a < n; ++a) order[a] = a;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+    for (int64_t a = 0; a < n; ++a) {
+        const int64_t v = vox[order[a]];
+        ijk[3 * a + 0] = (int32_t)(v % L->ni);
+        ijk[3 * a + 1] = (int32_t)((v / L->ni) % L->nj);
+        ijk[3 * a + 2] = (int32_t)(v / ((int64_t)L->ni * L->nj));
+        if (ids_out) ids_out[a] = ids[order[a]];
+    }
+    return PSC_OK;
+}
+
+int psc_unwrapped(psc_lattice* L, int32_t s, int32_t* xyz, uint32_t* ids_out, int64_t cap, int64_t* n_out)
+{
+    if (!L || !n_out || s < 0 || s >= L->nsp) return PSC_E_ARG;
+    if (!L->populated) return PSC_E_ORDER;
+    DevGuard dg(L->device);
+    std::vector<int32_t> vox;
+    std::vector<uint32_t> ids;
+    std::vector<uint64_t> img;
+    int rc = read_list(L, s, vox, ids, &img);
+    if (rc) return rc;
+    const int64_t n = (int64_t)vox.size();
+    *n_out = n;
+    if (n > cap || (n > 0 && !xyz)) return PSC_E_ARG;
+    std::vector<int64_t> order(n);
+    for (int64_t a = 0; a < n; ++a) order[a] = a;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+    for (int64_t a = 0; a < n; ++a) {
+        const int64_t v = vox[order[a]];
+        const uint64_t w = img[order[a]];
+        const int32_t i = (int32_t)(v % L->ni), j = (int32_t)((v / L->ni) % L->nj),
+                      k = (int32_t)(v / ((int64_t)L->ni * L->nj));
+        const int32_t I = i + (int32_t)(int16_t)(w & 0xFFFF) * L->ni;
+        const int32_t J = j + (int32_t)(int16_t)((w >> 16) & 0xFFFF) * L->nj;
+        const int32_t K = k + (int32_t)(int16_t)((w >> 32) & 0xFFFF) * L->nk;
+        xyz[3 * a + 0] = 2 * I + ((J + K) & 1);
+        xyz[3 * a + 1] = 3 * J + (K & 1);
+        xyz[3 * a + 2] = K;
+        if (ids_out) ids_out[a] = ids[order[a]];
+    }
+    return PSC_OK;
+}
+
+int psc_grid(psc_lattice* L, uint16_t* occ)
+{
+    if (!L || !occ) return PSC_E_ARG;
+    if (!L->populated) return PSC_E_ORDER;
+    DevGuard dg(L->device);
+    int rc = check_device(L);
+    if (rc) return rc;
+    return cuda_fail(L, cudaMemcpy(occ, L->occ, (size_t)L->V * 2, cudaMemcpyDeviceToHost));
+}
+
+int psc_time(const psc_lattice* L, double* t)
+{
+    if (!L || !t) return PSC_E_ARG;
+    *t = L->clock;
+    return PSC_OK;
+}
+
+int psc_event_index(const psc_lattice* L, uint32_t* g)
+{
+    if (!L || !g) return PSC_E_ARG;
+    *g = L->g;
+    return PSC_OK;
+}
+
+int psc_stats_get(psc_lattice* L, psc_stats* out)
+{
+    if (!L || !out) return PSC_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->events = L->events;
+    out->launches = (uint64_t)L->launches;
+    if (!L->populated) return PSC_OK;
+    DevGuard dg(L->device);
+    int rc = check_device(L);
+    if (rc) return rc;
+    unsigned long long st[kNumStats];
+    if ((rc = cuda_fail(L, cudaMemcpy(st, L->sc->stats, sizeof(st), cudaMemcpyDeviceToHost)))) return rc;
+    out->attempts = st[kStatAttempts];
+    out->hops = st[kStatHops];
+    out->collisions = st[kStatCollisions];
+    out->accepted = st[kStatAccepted];
+    out->reactions2 = st[kStatReactions2];
+    out->fires = st[kStatFires];
+    out->reactions1 = st[kStatReactions1];
+    out->births = st[kStatBirths];
+    return PSC_OK;
+}
+
+int psc_set_options(psc_lattice* L, const psc_options* o)
+{
+    if (!L || !o) return PSC_E_ARG;
+    if (o->block_threads && (o->block_threads < 32 || o->block_threads > 256 || (o->block_threads & 31)))
+        return PSC_E_ARG;
+    if (o->blocks_per_sm < 0 || o->graph_events < 0) return PSC_E_ARG;
+    if (o->resort_period) L->opt.resort_period = o->resort_period;
+    if (o->block_threads) L->opt.block_threads = o->block_threads;
+    if (o->blocks_per_sm) L->opt.blocks_per_sm = o->blocks_per_sm;
+    if (o->collect_stats) L->opt.collect_stats = o->collect_stats;
+    if (o->graph_events) L->opt.graph_events = o->graph_events;
+    return PSC_OK;
+}
+
+int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
+{
+    if (!L || !bytes) return PSC_E_ARG;
+    int64_t b = L->V * 6 + (int64_t)sizeof(Scalars) + (int64_t)sizeof(ModelDev);
+    int64_t N = 0;
+    for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
+    if (L->populated) {
+        int64_t mx = 1, mm = 1;
+        for (int s = 0; s < L->nsp; ++s) {
+            b += (int64_t)L->cap[s] * 16;
+            mx = std::max<int64_t>(mx, L->cap[s]);
+            if (L->sp[s].D > 0.0) mm = std::max<int64_t>(mm, L->cap[s]);
+        }
+        b += mx * 16 + (int64_t)L->births_cap * (int64_t)sizeof(Birth) + mm * 8 +
+             (int64_t)sort_scratch_bytes(mm);
+    } else {
+        b += 2 * N * 16 + 2 * N * 8;
+    }
+    *bytes = b;
+    return PSC_OK;
+}
+
+void psc_lattice_destroy(psc_lattice* L)
+{
+    if (!L) return;
+    {
+        DevGuard dg(L->device);
+        if (L->stream) cudaStreamSynchronize(L->stream);
+        dev_free_all(L);
+        if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+    }
+    delete L;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// psc_internal.h -- device-side data layout and launch interfaces of the hop
+// engine.  Shared by the CUDA translation units and the host runtime; not part
+// of the public ABI (include/psc.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace psc {
+
+constexpr int kMaxSpecies = 32;
+constexpr int kMaxReactions = 128;
+constexpr int kMaxFirstOrder = 8;          // first-order reactions per species
+constexpr uint32_t kNoClaim = 0xFFFFFFFFu;  // claim word of an unclaimed voxel
+constexpr uint16_t kBlocked = 0xFFFFu;      // occupancy code reserved for walls
+constexpr uint32_t kTagEvent = 0u;          // Philox counter word 2 domain tags
+constexpr uint32_t kTagPopulate = 1u;
+
+// Error bits raised on the device, read back by psc_synchronize.
+constexpr int32_t kErrListOverflow = 1;
+constexpr int32_t kErrBirthOverflow = 2;
+
+// n / d for n, d < 2^31 by one high multiply (round-up reciprocal).
+struct FastDiv {
+    uint32_t d;
+    uint32_t m;
+    int32_t s;  // -1 marks d == 1
+};
+FastDiv make_fastdiv(uint32_t d);
+
+struct Geometry {
+    int32_t ni, nj, nk;
+    uint32_t bflags;      // bit a set: axis a periodic
+    uint32_t ninj;
+    FastDiv div_ni;
+    FastDiv div_ninj;
+};
+
+// Structure-of-arrays list of the molecules of one species.  img packs three
+// 16-bit periodic wrap counters (i at bits 0-15, j at 16-31, k at 32-47).
+struct SpeciesList {
+    int32_t* vox;
+    uint32_t* ids;
+    uint64_t* img;
+    int32_t cap;
+};
+
+struct ReactionDev {
+    uint64_t T;           // acceptance threshold (second order), floor(p 2^32)
+    int32_t np;           // products
+    int32_t p0, p1;       // product species
+};
+
+// Model tables, uploaded once at populate and read through a pointer.
+struct ModelDev {
+    int8_t pair[kMaxSpecies][kMaxSpecies];   // second-order reaction or -1
+    ReactionDev rx[kMaxReactions];
+    uint64_t T_fire[kMaxSpecies];            // first-order firing threshold
+    int32_t n_fo[kMaxSpecies];
+    int32_t fo_rx[kMaxSpecies][kMaxFirstOrder];
+    uint64_t fo_cum[kMaxSpecies][kMaxFirstOrder];
+    SpeciesList lists[kMaxSpecies];
+};
+
+enum StatIndex {
+    kStatAttempts = 0, kStatHops, kStatCollisions, kStatAccepted, kStatReactions2,
+    kStatFires, kStatReactions1, kStatBirths, kNumStats
+};
+
+// Small device-resident scalars of one lattice.
+struct Scalars {
+    int32_t counts[kMaxSpecies];     // molecules per species list
+    int32_t tmp_count[kMaxSpecies];  // survivors during a reconcile pass
+    uint32_t next_id;                // next fresh molecule id
+    int32_t births;                  // births queued in the current event
+    int32_t err;                     // kErr* bits
+    int32_t pad;
+    unsigned long long stats[kNumStats];
+};
+
+struct Birth {
+    uint32_t parent;
+    int32_t t;
+    int32_t species;
+    int32_t pad;
+    uint64_t img;
+};
+
+// Everything one event kernel needs, passed by value.
+struct EventArgs {
+    Geometry geo;
+    uint16_t* occ;
+    uint32_t* claim;
+    SpeciesList list;          // list of the due species
+    const int32_t* count;      // its length (device)
+    const ModelDev* model;
+    Scalars* sc;
+    Birth* births;
+    int32_t births_cap;
+    uint32_t key0, key1;       // Philox key = seed
+    uint32_t g;                // global event index
+    int32_t s;                 // due species
+    int32_t collect_stats;
+};
+
+struct ReconcileArgs {
+    uint16_t* occ;
+    int32_t x;                 // species whose list is reconciled
+    SpeciesList list;
+    SpeciesList tmp;
+    const ModelDev* model;
+    Scalars* sc;
+};
+
+// ---- launchers (psc_kernels.cu) ----
+void upload_stencil(cudaStream_t st);
+void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
+void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
+void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
+void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
+void launch_births(const EventArgs& a, cudaStream_t st);
+void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
+void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
+                          int blocks, cudaStream_t st);
+void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
+                             int n_species, uint16_t* occ, const ModelDev* model, int blocks,
+                             cudaStream_t st);
+void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
+                        uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st);
+void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32_t* perm,
+                    const int32_t* count, int blocks, cudaStream_t st);
+void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count,
+                      int blocks, cudaStream_t st);
+
+// ---- radix sort (psc_sort.cu) ----
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+// n is read from device memory (n_dev) or taken from n_host when n_dev is
+// null; max_n bounds it and sizes the scratch.
+struct SortScratch {
+    uint32_t* keys_alt = nullptr;
+    uint32_t* vals_alt = nullptr;
+    uint32_t* hist = nullptr;       // 256 * blocks
+    uint32_t* block_sums = nullptr; // scan partials
+    int64_t max_n = 0;
+    int64_t hist_len = 0;
+    int64_t sums_len = 0;
+};
+size_t sort_scratch_bytes(int64_t max_n);
+void sort_scratch_bind(SortScratch& s, void* base, int64_t max_n);
+// After the call the sorted data is in (keys, vals) again.
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, const int32_t* n_dev, int64_t n_host,
+                     int64_t max_n, int bits, SortScratch& scratch, cudaStream_t st,
+                     int64_t* launches);
+
+}  // namespace psc

@@ -1,0 +1,194 @@
+"""Bit-exact parity of the CUDA engine with the synchronous-rule oracle.
+
+Both sides get the same model and seed; at every checkpoint the occupancy
+grid, the counts, every molecule's (i, j, k) and unwrapped position sorted by
+id, the event index and the clock must be identical.  Sizes run from tiny and
+ragged shapes to the full 64^3 reaction case and the 512^3 diffusion lattice.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1605_03726_gb300 as psc
+import models
+
+pytestmark = pytest.mark.gpu
+
+
+def make_pair(shape, rv=1e-8, boundary=psc.PERIODIC_ALL, **opts):
+    g = psc.Lattice(*shape, voxel_radius=rv, boundary=boundary)
+    if opts:
+        g.set_options(**opts)
+    o = oracle.Lattice(*shape, rv, boundary, oracle.RULE_SYNC)
+    return g, o
+
+
+def assert_same(g, o, tag=""):
+    n = o.n_species
+    assert g.event_index() == o.event_index(), tag
+    assert g.time() == o.time(), tag
+    assert (g.counts() == o.counts()).all(), (tag, g.counts(), o.counts())
+    assert (g.grid() == o.grid()).all(), tag
+    for s in range(n):
+        gi, gid = g.coords(s)
+        oi, oid = o.coords(s)
+        assert np.array_equal(gid, oid), (tag, s)
+        assert np.array_equal(gi, oi), (tag, s)
+        gu, _ = g.unwrapped(s)
+        ou, _ = o.unwrapped(s)
+        assert np.array_equal(gu, ou), (tag, s)
+
+
+def build_both(shape, recipe, seed, boundary=psc.PERIODIC_ALL, rv=1e-8, **opts):
+    g, o = make_pair(shape, rv, boundary, **opts)
+    recipe(g)
+    recipe(o)
+    rg = g.populate(seed)
+    ro = o.populate(seed)
+    assert rg == ro
+    assert_same(g, o, "populate")
+    return g, o
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ab_to_c_64cubed_full_run(seed):
+    # 64^3 periodic, r_v 10 nm, A and B 2000 each (D 1 um^2/s), A + B -> C with
+    # k = 1e-19 m^3/s, C immobile; run to 1000 hop intervals of A
+    g, o = build_both((64, 64, 64), lambda L: models.reaction_diffusion_ab(L, 2000, 2000), seed)
+    tau = g.tau(0)
+    assert tau == o.tau(0)
+    assert g.p_ab(0) == o.p_ab(0)
+    for t in (1, 10, 100, 1000):
+        g.run(t * tau)
+        o.run(t * tau)
+        assert_same(g, o, "t=%d tau" % t)
+
+
+@pytest.mark.parametrize("shape,frac", [((96, 80, 64), 0.01), ((37, 24, 18), 0.30), ((50, 44, 30), 0.60)])
+def test_diffusion_ragged_shapes(shape, frac):
+    V = shape[0] * shape[1] * shape[2]
+    g, o = build_both(shape, lambda L: models.diffusion_only(L, int(frac * V)), 11, resort_period=7)
+    for _ in range(4):
+        g.run_events(13)
+        o.run_events(13)
+        assert_same(g, o)
+
+
+def test_reflective_crowded_reversible():
+    shape = (40, 36, 32)
+    V = 40 * 36 * 32
+    g, o = build_both(shape, lambda L: models.crowded_reversible(L, V, kb=2000.0), 5, boundary=0,
+                      collect_stats=1)
+    for _ in range(5):
+        g.run_events(60)
+        o.run_events(60)
+        assert_same(g, o)
+    sg, so = g.stats(), o.stats()
+    for key in ("attempts", "hops", "collisions", "accepted", "reactions2", "fires", "reactions1", "births"):
+        assert sg[key] == so[key], key
+    assert so["reactions2"] > 0 and so["births"] > 0
+
+
+def test_mapk_like_cascade():
+    shape = (40, 40, 40)
+    recipe = lambda L: models.mapk_like(L, 7, scale=0.3, uni_scale=300, bi_scale=3)
+    g, o = build_both(shape, recipe, 7, collect_stats=1)
+    for _ in range(6):
+        g.run_events(500)
+        o.run_events(500)
+        assert_same(g, o)
+    so = o.stats()
+    assert so["births"] > 50 and so["reactions2"] > 100
+    assert g.stats()["births"] == so["births"]
+
+
+@pytest.mark.parametrize("products", [[], [2], [2, 3]])
+def test_second_order_product_counts(products):
+    def recipe(L):
+        a = L.add_species(2e-12, 1500)
+        b = L.add_species(1e-12, 1500)
+        L.add_species(0.5e-12, 0)
+        L.add_species(0.0, 0)
+        L.add_reaction([a, b], products, 5e-19)
+    g, o = build_both((32, 32, 32), recipe, 9)
+    for _ in range(3):
+        g.run_events(40)
+        o.run_events(40)
+        assert_same(g, o)
+
+
+@pytest.mark.parametrize("products", [[], [1], [1, 2], [0, 2]])
+def test_first_order_product_counts(products):
+    def recipe(L):
+        a = L.add_species(1e-12, 3000)
+        L.add_species(0.3e-12, 0)
+        L.add_species(0.0, 0)
+        L.add_reaction([a], products, 3000.0)
+    g, o = build_both((24, 24, 24), recipe, 4)
+    for _ in range(3):
+        g.run_events(25)
+        o.run_events(25)
+        assert_same(g, o)
+
+
+def test_edge_cases():
+    # empty lattice
+    g, o = build_both((8, 8, 8), lambda L: L.add_species(1e-12, 0), 1)
+    g.run_events(3); o.run_events(3)
+    assert_same(g, o, "empty")
+    # full lattice: nothing can move
+    g, o = build_both((6, 6, 6), lambda L: L.add_species(1e-12, 216), 1)
+    g.run_events(3); o.run_events(3)
+    assert_same(g, o, "full")
+    # single molecule on the smallest periodic lattice
+    g, o = build_both((3, 4, 4), lambda L: L.add_species(1e-12, 1), 2)
+    g.run_events(50); o.run_events(50)
+    assert_same(g, o, "single")
+    # one voxel, reflective: every hop hits a wall
+    g, o = build_both((1, 1, 1), lambda L: L.add_species(1e-12, 1), 3, boundary=0)
+    g.run_events(5); o.run_events(5)
+    assert_same(g, o, "one voxel")
+    # only immobile species: no events at all
+    g, o = build_both((8, 8, 8), lambda L: L.add_species(0.0, 100), 4)
+    g.run(1.0); o.run(1.0)
+    assert_same(g, o, "immobile")
+    # mixed boundaries, odd reflective extents
+    g, o = build_both((7, 9, 8), lambda L: L.add_species(1e-12, 150), 5, boundary=psc.PERIODIC_K)
+    g.run_events(30); o.run_events(30)
+    assert_same(g, o, "mixed")
+
+
+def test_results_do_not_depend_on_launch_shape_or_resort():
+    recipe = lambda L: models.reaction_diffusion_ab(L, 3000, 3000, k=3e-19)
+    states = []
+    for opts in (dict(resort_period=-1), dict(resort_period=1), dict(block_threads=64, blocks_per_sm=1),
+                 dict(block_threads=128, blocks_per_sm=3, resort_period=5)):
+        g = psc.Lattice(48, 48, 48)
+        g.set_options(**opts)
+        recipe(g)
+        g.populate(21)
+        g.run_events(120)
+        states.append((g.grid(), [g.coords(s) for s in range(3)]))
+    for grid, coords in states[1:]:
+        assert np.array_equal(grid, states[0][0])
+        for (a, b), (c, d) in zip(coords, states[0][1]):
+            assert np.array_equal(a, c) and np.array_equal(b, d)
+
+
+def test_diffusion_256cubed_one_percent():
+    g, o = build_both((256, 256, 256), lambda L: models.diffusion_only(L, 167772), 2)
+    for _ in range(2):
+        g.run_events(10)
+        o.run_events(10)
+        assert_same(g, o)
+
+
+@pytest.mark.slow
+def test_diffusion_512cubed_full_size():
+    # the 512^3 lattice at 1 % occupancy (1,342,177 molecules, D = 10 um^2/s) in
+    # the launch configuration the benchmark times
+    n = int(0.01 * 512 ** 3)
+    g, o = build_both((512, 512, 512), lambda L: models.diffusion_only(L, n, D=10e-12), 1)
+    g.run_events(3)
+    o.run_events(3)
+    assert_same(g, o)

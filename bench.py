@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the voxel hop step (pSpatiocyte, arXiv:1605.03726, Sec. 2.3).
+
+Workload: 512 x 512 x 512 HCP lattice, periodic, r_v = 10 nm, one species with
+D = 10 um^2/s at 1 % occupancy (1,342,177 molecules placed uniformly from the
+seed), diffusion only.  One benchmark step = 100 hop intervals (100 events of
+the species, one Morton re-sort of its list); the default 100 timed steps are
+the 10^4 events of the 512^3 case.  Metric: molecule hop-attempts per second
+(one attempt = one molecule processed in one event, whatever the outcome).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Each GPU (rank) runs its own replica of the lattice (seed 1 + rank); replicas
+share nothing, so the job scales weakly with no collective on the data path.
+--impl reference times the plain CPU oracle (synchronous rule) on the host
+cores instead, one event of the same lattice per step.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SHAPE = (512, 512, 512)
+RV = 1e-8
+D = 10e-12
+OCCUPANCY = 0.01
+N_MOL = int(OCCUPANCY * SHAPE[0] * SHAPE[1] * SHAPE[2])   # 1,342,177
+EVENTS_PER_STEP = 100
+RESORT_PERIOD = 100
+METRIC = "molecule hop-attempts/s"
+UNIT = "attempts/s"
+WORKLOAD = ("512^3 HCP lattice, periodic, r_v=10nm, 1 species D=10um^2/s at 1% occupancy "
+            "(1,342,177 molecules), diffusion only; step = 100 hop intervals")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="psc_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_attempt():
+    """DRAM bytes per hop attempt of the claim + commit pair from the committed
+    ncu summary, or None (the file is written after each profile of the kernels)."""
+    p = os.path.join(ROOT, "profiles", "hop_step_512cubed_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d
+    except Exception:
+        return None
+
+
+def make_lattice(psc, seed, device, stream):
+    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=device, stream=stream)
+    L.add_species(D, N_MOL)
+    L.set_options(resort_period=RESORT_PERIOD)
+    L.populate(seed)
+    return L
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+
+    import paper_1605_03726_gb300 as psc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream(device=local)
+    L = make_lattice(psc, 1 + rank, local, stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        L.run_events(EVENTS_PER_STEP)
+    L.synchronize()
+
+    # timed region: K steps on the library's stream, CUDA events on that stream
+    L.set_options(time_kernels=1)
+    L.kernel_times()                       # drop anything recorded so far
+    launches0 = L.stats()["launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        L.run_events(EVENTS_PER_STEP)
+    ev1.record(stream)
+    torch.cuda.synchronize(local)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kt = L.kernel_times()
+    launches = L.stats()["launches"] - launches0
+    L.set_options(time_kernels=-1)
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    attempts = args.steps * EVENTS_PER_STEP * N_MOL * world
+    value = attempts / (elapsed_ms * 1e-3)
+
+    # success fraction of the hops, from a short counted run after the timed region
+    L.set_options(collect_stats=1)
+    st0 = L.stats()
+    L.run_events(20)
+    st1 = L.stats()
+    L.set_options(collect_stats=-1)
+    s_frac = (st1["hops"] - st0["hops"]) / max(1, st1["attempts"] - st0["attempts"])
+
+    # roofline of the hop step: claim + commit kernels of one event
+    hbm, peak_kind = peaks()
+    b_alg = 14.0 + 8.0 * s_frac            # bytes per attempt
+    n_ev = max(1, kt["claim_launches"])
+    t_event_ms = (kt["claim_ms"] + kt["commit_ms"]) / n_ev
+    achieved = b_alg * N_MOL / (t_event_ms * 1e-3) / 1e9
+    tr = traffic_per_attempt()
+    traffic = None
+    if tr and tr.get("kernel_rev") == kernel_revision():
+        traffic = tr["bytes_per_event"]
+    roofline = {
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+        "frac": round(achieved / hbm, 4), "traffic": traffic,
+        "kernel": "k_claim + k_commit (one hop event over all molecules)",
+        "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+        "bytes_alg_per_attempt": round(b_alg, 3), "hop_success": round(s_frac, 5),
+        "event_us": round(t_event_ms * 1e3, 3),
+        "claim_us": round(kt["claim_ms"] / n_ev * 1e3, 3),
+        "commit_us": round(kt["commit_ms"] / n_ev * 1e3, 3),
+        "resort_us": round(kt["resort_ms"] / max(1, kt["resorts"]) * 1e3, 3),
+        "share_of_step": round((kt["claim_ms"] + kt["commit_ms"]) / max(1e-9, elapsed_ms), 4),
+    }
+    L.close()
+    res = {"value": value, "elapsed_ms": elapsed_ms, "roofline": roofline, "clocks": clocks,
+           "gpu_launches": int(launches)}
+
+    if not args.no_e2e:
+        res["e2e"] = e2e_run(psc, args, rank, local, torch)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return res
+
+
+def kernel_revision():
+    """Hash of the kernel sources: ncu traffic is reported only for the kernels it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("psc_kernels.cu", "psc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1605_03726_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def e2e_run(psc, args, rank, local, torch):
+    """The whole job through the C ABI with host buffers: create, populate,
+    K steps each followed by a read of the species counts into host memory,
+    final positions read back, destroy."""
+    torch.cuda.synchronize(local)
+    t0 = time.perf_counter()
+    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=local)
+    L.add_species(D, N_MOL)
+    L.set_options(resort_period=RESORT_PERIOD)
+    L.populate(1 + rank)
+    for _ in range(args.steps):
+        L.run_events(EVENTS_PER_STEP)
+        c = L.counts()
+    ijk, ids = L.coords(0)
+    st = L.stats()
+    L.close()
+    t1 = time.perf_counter()
+    assert int(c[0]) == N_MOL and len(ids) == N_MOL
+    steps = max(1, args.steps)
+    return {"value": args.steps * EVENTS_PER_STEP * N_MOL / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": int(st["h2d_bytes"] // steps),
+            "d2h_bytes_per_step": int(st["d2h_bytes"] // steps),
+            "includes": "lattice create + populate (placement sort of 134M voxels) + K steps, "
+                        "counts read to host after every step, final positions read to host"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_lattice(seed):
+    import oracle
+    L = oracle.Lattice(*SHAPE, RV, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
+    L.add_species(D, N_MOL)
+    L.populate(seed)
+    return L
+
+
+def cpu_baseline(seconds):
+    t0 = time.perf_counter()
+    L = oracle_lattice(1)
+    t_pop = time.perf_counter() - t0
+    L.run_events(1)                                    # calibrate
+    t1 = time.perf_counter()
+    L.run_events(1)
+    per_event = time.perf_counter() - t1
+    n = max(1, int(seconds / max(per_event, 1e-3)))
+    t2 = time.perf_counter()
+    L.run_events(n)
+    dt = time.perf_counter() - t2
+    L.close()
+    return {"value": n * N_MOL / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d events of the 512^3 lattice (%d attempts each) after its populate (%.1f s, untimed), "
+                      "single thread, %s" % (n, N_MOL, t_pop, cpu_model())}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    L = oracle_lattice(1)
+    for _ in range(args.warmup):
+        L.run_events(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.run_events(1)
+    dt = time.perf_counter() - t0
+    L.close()
+    value = args.steps * N_MOL / dt
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "1 hop interval (oracle)", "lattice": list(SHAPE),
+                   "molecules": N_MOL},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d + %d warm-up events of the 512^3 lattice, single thread, %s"
+                                   % (args.steps, args.warmup, cpu_model())},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    res = gpu_arm(args, rank, world, local)
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["elapsed_ms"] / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(SHAPE), "molecules": N_MOL,
+                   "events_per_step": EVENTS_PER_STEP, "resort_period": RESORT_PERIOD,
+                   "replicas": world, "l2": "inputs larger than L2 (occupancy 268 MB + claim words 537 MB)",
+                   "parallelism": "replicas (one independent lattice per GPU)"},
+        "roofline": res["roofline"],
+        "gpu_launches": res["gpu_launches"],
+        "clocks": res["clocks"],
+    }
+    if "e2e" in res:
+        out["e2e"] = res["e2e"]
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -97,7 +97,16 @@ typedef struct {
     uint64_t attempts, hops, collisions, accepted, reactions2, fires, reactions1, births;
     uint64_t events;          /* species events queued                         */
     uint64_t launches;        /* kernels launched by this lattice (host count) */
+    uint64_t h2d_bytes;       /* bytes copied host -> device by the library    */
+    uint64_t d2h_bytes;       /* bytes copied device -> host by the library    */
 } psc_stats;
+
+/* Device time of the event kernels, measured with CUDA events recorded on the
+   lattice's stream around each launch while psc_options.time_kernels is on. */
+typedef struct {
+    double claim_ms, commit_ms, reconcile_ms, resort_ms;
+    int64_t claim_launches, commit_launches, reconcile_events, resorts;
+} psc_kernel_times;
 
 /* Tunables; zero in a field keeps the current value. */
 typedef struct {
@@ -108,6 +117,10 @@ typedef struct {
     int32_t collect_stats;    /* 1 = count attempts/hops/... (default 0), -1 off */
     int32_t graph_events;     /* >0: replay runs of this many single-species
                                  events from a captured CUDA graph (default 0) */
+    int32_t time_kernels;     /* 1 = record CUDA events around the kernels of
+                                 every event (psc_kernel_times_get), -1 off     */
+    int32_t claim_table;      /* before populate: 1 = one claim word per voxel,
+                                 2 = hash table of claims, 0/-1 = by size      */
 } psc_options;
 
 /*
@@ -192,6 +205,10 @@ int psc_event_index(const psc_lattice *L, uint32_t *g);
 
 /* Device counters (see psc_stats).  Synchronises. */
 int psc_stats_get(psc_lattice *L, psc_stats *s);
+
+/* Sum of the kernel times recorded since the last call (and reset them).
+   Synchronises. */
+int psc_kernel_times_get(psc_lattice *L, psc_kernel_times *out);
 
 /* Change tunables (psc_options); allowed at any time between calls. */
 int psc_set_options(psc_lattice *L, const psc_options *opt);

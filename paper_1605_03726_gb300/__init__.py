@@ -25,7 +25,7 @@ _lib = None
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "attempts", "hops", "collisions", "accepted", "reactions2", "fires", "reactions1", "births",
-        "events", "launches")]
+        "events", "launches", "h2d_bytes", "d2h_bytes")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -33,7 +33,19 @@ class Stats(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events")]
+        "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
+        "claim_table")]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("claim_ms", ctypes.c_double), ("commit_ms", ctypes.c_double),
+                ("reconcile_ms", ctypes.c_double), ("resort_ms", ctypes.c_double),
+                ("claim_launches", ctypes.c_int64), ("commit_launches", ctypes.c_int64),
+                ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))
+                for n, t in self._fields_}
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
@@ -67,6 +79,7 @@ def lib():
             "psc_event_index": (ctypes.c_int, [P, ctypes.POINTER(u32)]),
             "psc_stats_get": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
             "psc_set_options": (ctypes.c_int, [P, ctypes.POINTER(Options)]),
+            "psc_kernel_times_get": (ctypes.c_int, [P, ctypes.POINTER(KernelTimes)]),
             "psc_tau": (dbl, [P, i32]),
             "psc_p_ab": (dbl, [P, i32]),
             "psc_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
@@ -84,7 +97,8 @@ def lib():
 
 EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_populate", "psc_run",
             "psc_run_events", "psc_synchronize", "psc_counts", "psc_coords", "psc_unwrapped", "psc_grid",
-            "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_tau", "psc_p_ab",
+            "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_kernel_times_get",
+            "psc_tau", "psc_p_ab",
             "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator")
 
 
@@ -232,6 +246,11 @@ class Lattice:
         s = Stats()
         _check("psc_stats_get", lib().psc_stats_get(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+    def kernel_times(self):
+        k = KernelTimes()
+        _check("psc_kernel_times_get", lib().psc_kernel_times_get(self._h, ctypes.byref(k)))
+        return k.as_dict()
 
     def tau(self, species):
         return lib().psc_tau(self._h, species)

@@ -87,7 +87,12 @@ struct psc_lattice {
     ModelDev model_h{};
     ModelDev* model_d = nullptr;
     uint16_t* occ = nullptr;
-    uint32_t* claim = nullptr;
+    uint32_t* bits = nullptr;          // vacancy mirror, one bit per voxel
+    uint32_t* claim = nullptr;         // per-voxel claim words (small lattices)
+    uint64_t* tables[2] = {nullptr, nullptr};   // claim hash tables (large lattices)
+    uint32_t table_used[2] = {0, 0};   // slots written by the event that used it
+    int64_t table_slots = 0;
+    uint32_t hash_bits[kMaxSpecies] = {};
     Scalars* sc = nullptr;
     Birth* births = nullptr;
     int32_t births_cap = 0;
@@ -99,13 +104,20 @@ struct psc_lattice {
     int64_t rs_max = 0;
 
     bool general[kMaxSpecies] = {};
+    bool live[kMaxSpecies] = {};       // takes part in a reaction: keeps its codes
     bool fo2[kMaxSpecies] = {};
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 0};
+    psc_options opt{64, 256, 8, 0, 0, 0, 0};
     int64_t launches = 0;
     uint64_t events = 0;
+    uint64_t h2d = 0, d2h = 0;
+
+    // CUDA-event spans around kernels (psc_options.time_kernels)
+    struct Span { cudaEvent_t a, b; int kind; };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;
     int sticky = PSC_OK;
     std::vector<void*> allocs;
 };
@@ -166,7 +178,16 @@ EventArgs event_args(const psc_lattice* L, int s)
     EventArgs a{};
     a.geo = L->geo;
     a.occ = L->occ;
-    a.claim = L->claim;
+    a.bits = L->bits;
+    a.ct.direct = L->claim;
+    if (L->tables[0]) {
+        const int cur = (int)(L->g & 1u), other = cur ^ 1;
+        a.ct.hash = L->tables[cur];
+        a.ct.hash_bits = L->hash_bits[s];
+        a.ct.clear = L->tables[other];
+        a.ct.clear_n = L->table_used[other];
+    }
+    a.live = L->live[s] ? 1 : 0;
     a.list = L->model_h.lists[s];
     a.count = &L->sc->counts[s];
     a.model = L->model_d;
@@ -179,6 +200,38 @@ EventArgs event_args(const psc_lattice* L, int s)
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;
+}
+
+enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort };
+
+cudaEvent_t take_event(psc_lattice* L)
+{
+    if (!L->event_pool.empty()) {
+        cudaEvent_t e = L->event_pool.back();
+        L->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// open a span: returns its start event (recorded now) or null when timing is off
+cudaEvent_t span_open(psc_lattice* L)
+{
+    if (L->opt.time_kernels <= 0) return nullptr;
+    cudaEvent_t a = take_event(L);
+    if (a) cudaEventRecord(a, L->stream);
+    return a;
+}
+
+void span_close(psc_lattice* L, cudaEvent_t a, int kind)
+{
+    if (!a) return;
+    cudaEvent_t b = take_event(L);
+    if (!b) { L->event_pool.push_back(a); return; }
+    cudaEventRecord(b, L->stream);
+    L->spans.push_back({a, b, kind});
 }
 
 int resort(psc_lattice* L, int s)
@@ -201,12 +254,23 @@ int enqueue_event(psc_lattice* L, int s)
     const EventArgs a = event_args(L, s);
     const int threads = L->opt.block_threads;
     const int blocks = event_blocks(L, L->cap[s]);
+    cudaEvent_t sp = span_open(L);
     launch_claim(a, L->general[s], blocks, threads, L->stream);
+    span_close(L, sp, kSpanClaim);
+    sp = span_open(L);
     launch_commit(a, L->general[s], blocks, threads, L->stream);
+    span_close(L, sp, kSpanCommit);
     L->launches += 2;
+    if (L->tables[0]) {
+        const int cur = (int)(L->g & 1u);
+        L->table_used[cur] = 1u << L->hash_bits[s];
+        L->table_used[cur ^ 1] = 0;
+    }
+    sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
     for (int x : L->reconcile[s]) {
         ReconcileArgs r{};
         r.occ = L->occ;
+        r.bits = L->bits;
         r.x = x;
         r.list = L->model_h.lists[x];
         r.tmp = L->tmp;
@@ -221,10 +285,13 @@ int enqueue_event(psc_lattice* L, int s)
         launch_births(a, L->stream);
         L->launches += 1;
     }
+    span_close(L, sp, kSpanReconcile);
     L->events++;
     if (L->opt.resort_period > 0 && ++L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
         L->since_resort[s] = 0;
+        sp = span_open(L);
         int rc = resort(L, s);
+        span_close(L, sp, kSpanResort);
         if (rc) return rc;
     }
     return cuda_fail(L, cudaPeekAtLastError());
@@ -254,6 +321,7 @@ int check_device(psc_lattice* L)
     int32_t err = 0;
     e = cudaMemcpy(&err, &L->sc->err, sizeof(err), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(L, e);
+    L->d2h += sizeof(err);
     if (err) L->sticky = PSC_E_CAPACITY;
     return L->sticky;
 }
@@ -447,6 +515,11 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         }
     }
     // ---- which lists an event can touch ----
+    for (int s = 0; s < L->nsp; ++s) L->live[s] = false;
+    for (int r = 0; r < L->nrx; ++r) {
+        for (int a = 0; a < L->rx[r].nr; ++a) L->live[L->rx[r].r[a]] = true;
+        for (int a = 0; a < L->rx[r].np; ++a) L->live[L->rx[r].p[a]] = true;
+    }
     for (int s = 0; s < L->nsp; ++s) {
         bool so = false;
         L->reconcile[s].clear();
@@ -476,11 +549,34 @@ int psc_populate(psc_lattice* L, uint64_t seed)
 
     // ---- device memory ----
     const size_t V = (size_t)L->V;
+    const size_t nwords = ((size_t)L->V + 31) / 32;
     L->occ = (uint16_t*)dev_alloc(L, V * sizeof(uint16_t));
-    L->claim = (uint32_t*)dev_alloc(L, V * sizeof(uint32_t));
+    L->bits = (uint32_t*)dev_alloc(L, nwords * sizeof(uint32_t));
     L->sc = (Scalars*)dev_alloc(L, sizeof(Scalars));
     L->model_d = (ModelDev*)dev_alloc(L, sizeof(ModelDev));
-    if (!L->occ || !L->claim || !L->sc || !L->model_d) return PSC_E_NOMEM;
+    if (!L->occ || !L->bits || !L->sc || !L->model_d) return PSC_E_NOMEM;
+    // claims: a word per voxel on small lattices, else two hash tables with at
+    // least two slots per molecule of the largest mobile species
+    uint32_t hb_max = 0;
+    for (int s = 0; s < L->nsp; ++s) {
+        uint32_t hb = 10;
+        while (hb < 31 && (1ll << hb) < 2ll * L->cap[s]) ++hb;
+        L->hash_bits[s] = hb;
+        if (L->sp[s].D > 0.0 && hb > hb_max) hb_max = hb;
+    }
+    bool direct = L->V <= (1ll << 22) || hb_max == 0;
+    if (L->opt.claim_table == 1) direct = true;
+    if (L->opt.claim_table == 2 && hb_max > 0) direct = false;
+    if (direct) {
+        L->claim = (uint32_t*)dev_alloc(L, V * sizeof(uint32_t));
+        if (!L->claim) return PSC_E_NOMEM;
+    } else {
+        L->table_slots = (int64_t)1 << hb_max;
+        for (int t = 0; t < 2; ++t) {
+            L->tables[t] = (uint64_t*)dev_alloc(L, ((size_t)1 << hb_max) * sizeof(uint64_t));
+            if (!L->tables[t]) return PSC_E_NOMEM;
+        }
+    }
     for (int s = 0; s < L->nsp; ++s) {
         SpeciesList& l = M.lists[s];
         l.cap = L->cap[s];
@@ -507,14 +603,18 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     upload_stencil(st);
     int rc = cuda_fail(L, cudaMemcpyAsync(L->model_d, &M, sizeof(M), cudaMemcpyHostToDevice, st));
     if (rc) return rc;
+    L->h2d += sizeof(M) + 5 * sizeof(uint32_t) + sizeof(Scalars);
     Scalars sh;
     std::memset(&sh, 0, sizeof(sh));
     for (int s = 0; s < L->nsp; ++s) sh.counts[s] = (int32_t)L->sp[s].n0;
     sh.next_id = (uint32_t)N;
     if ((rc = cuda_fail(L, cudaMemcpyAsync(L->sc, &sh, sizeof(sh), cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->occ, 0, V * sizeof(uint16_t), st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->bits, 0, nwords * sizeof(uint32_t), st)))) return rc;
     const int fill_blocks = L->sm_count * 8;
-    launch_fill_u32(L->claim, kNoClaim, V, fill_blocks, st);
+    if (L->claim) launch_fill_u32(L->claim, kNoClaim, V, fill_blocks, st);
+    for (int t = 0; t < 2; ++t)
+        if (L->tables[t]) launch_fill_u64(L->tables[t], kEmptySlot, (size_t)1 << hb_max, fill_blocks, st);
 
     // ---- placement: voxels sorted by (Philox key, voxel) dealt to the species ----
     if (N > 0) {
@@ -530,7 +630,7 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         int64_t off[kMaxSpecies + 1];
         off[0] = 0;
         for (int s = 0; s < L->nsp; ++s) off[s + 1] = off[s] + L->sp[s].n0;
-        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->model_d, fill_blocks, st);
+        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->bits, L->model_d, fill_blocks, st);
         if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
         dev_free_one(L, keys);
         dev_free_one(L, vals);
@@ -601,6 +701,7 @@ int psc_counts(psc_lattice* L, int64_t* counts, int32_t n)
     if (rc) return rc;
     int32_t c[kMaxSpecies];
     if ((rc = cuda_fail(L, cudaMemcpy(c, L->sc->counts, sizeof(c), cudaMemcpyDeviceToHost)))) return rc;
+    L->d2h += sizeof(c);
     for (int s = 0; s < L->nsp; ++s) counts[s] = c[s];
     return PSC_OK;
 }
@@ -612,6 +713,7 @@ static int read_list(psc_lattice* L, int32_t s, std::vector<int32_t>& vox, std::
     if (rc) return rc;
     int32_t n = 0;
     if ((rc = cuda_fail(L, cudaMemcpy(&n, &L->sc->counts[s], 4, cudaMemcpyDeviceToHost)))) return rc;
+    L->d2h += 4 + (uint64_t)n * (img ? 16 : 8);
     const SpeciesList& l = L->model_h.lists[s];
     vox.resize(n);
     ids.resize(n);
@@ -690,7 +792,22 @@ int psc_grid(psc_lattice* L, uint16_t* occ)
     DevGuard dg(L->device);
     int rc = check_device(L);
     if (rc) return rc;
-    return cuda_fail(L, cudaMemcpy(occ, L->occ, (size_t)L->V * 2, cudaMemcpyDeviceToHost));
+    // exact codes: mirror-masked codes of species with reactions, then the
+    // species without reactions from their lists
+    uint16_t* tmp = (uint16_t*)dev_alloc(L, (size_t)L->V * 2);
+    if (!tmp) return PSC_E_NOMEM;
+    const int blocks = L->sm_count * 8;
+    launch_materialize(tmp, L->occ, L->bits, L->V, blocks, L->stream);
+    for (int s = 0; s < L->nsp; ++s)
+        if (!L->live[s])
+            launch_scatter_codes(tmp, L->model_h.lists[s], &L->sc->counts[s], (uint16_t)(s + 1), blocks,
+                                 L->stream);
+    L->launches += 1;
+    rc = cuda_fail(L, cudaStreamSynchronize(L->stream));
+    if (!rc) rc = cuda_fail(L, cudaMemcpy(occ, tmp, (size_t)L->V * 2, cudaMemcpyDeviceToHost));
+    L->d2h += (uint64_t)L->V * 2;
+    dev_free_one(L, tmp);
+    return rc;
 }
 
 int psc_time(const psc_lattice* L, double* t)
@@ -713,12 +830,15 @@ int psc_stats_get(psc_lattice* L, psc_stats* out)
     std::memset(out, 0, sizeof(*out));
     out->events = L->events;
     out->launches = (uint64_t)L->launches;
+    out->h2d_bytes = L->h2d;
+    out->d2h_bytes = L->d2h;
     if (!L->populated) return PSC_OK;
     DevGuard dg(L->device);
     int rc = check_device(L);
     if (rc) return rc;
     unsigned long long st[kNumStats];
     if ((rc = cuda_fail(L, cudaMemcpy(st, L->sc->stats, sizeof(st), cudaMemcpyDeviceToHost)))) return rc;
+    L->d2h += sizeof(st);
     out->attempts = st[kStatAttempts];
     out->hops = st[kStatHops];
     out->collisions = st[kStatCollisions];
@@ -741,13 +861,44 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
     if (o->blocks_per_sm) L->opt.blocks_per_sm = o->blocks_per_sm;
     if (o->collect_stats) L->opt.collect_stats = o->collect_stats;
     if (o->graph_events) L->opt.graph_events = o->graph_events;
+    if (o->time_kernels) L->opt.time_kernels = o->time_kernels;
+    if (o->claim_table) {
+        if (o->claim_table < -1 || o->claim_table > 2) return PSC_E_ARG;
+        if (L->populated) return PSC_E_ORDER;
+        L->opt.claim_table = o->claim_table;
+    }
+    return PSC_OK;
+}
+
+int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
+{
+    if (!L || !out) return PSC_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    DevGuard dg(L->device);
+    cudaError_t e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) return cuda_fail(L, e);
+    for (const auto& sp : L->spans) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) != cudaSuccess) ms = 0.0f;
+        switch (sp.kind) {
+        case kSpanClaim: out->claim_ms += ms; out->claim_launches++; break;
+        case kSpanCommit: out->commit_ms += ms; out->commit_launches++; break;
+        case kSpanReconcile: out->reconcile_ms += ms; out->reconcile_events++; break;
+        default: out->resort_ms += ms; out->resorts++; break;
+        }
+        L->event_pool.push_back(sp.a);
+        L->event_pool.push_back(sp.b);
+    }
+    L->spans.clear();
     return PSC_OK;
 }
 
 int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
 {
     if (!L || !bytes) return PSC_E_ARG;
-    int64_t b = L->V * 6 + (int64_t)sizeof(Scalars) + (int64_t)sizeof(ModelDev);
+    int64_t b = L->V * 2 + (L->V + 31) / 32 * 4 + (int64_t)sizeof(Scalars) + (int64_t)sizeof(ModelDev);
+    if (L->claim) b += L->V * 4;
+    b += 2 * L->table_slots * 8;
     int64_t N = 0;
     for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
     if (L->populated) {
@@ -772,6 +923,8 @@ void psc_lattice_destroy(psc_lattice* L)
     {
         DevGuard dg(L->device);
         if (L->stream) cudaStreamSynchronize(L->stream);
+        for (const auto& sp : L->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+        for (cudaEvent_t ev : L->event_pool) cudaEventDestroy(ev);
         dev_free_all(L);
         if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     }

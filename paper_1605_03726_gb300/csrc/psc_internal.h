@@ -21,6 +21,7 @@ constexpr uint32_t kTagPopulate = 1u;
 // Error bits raised on the device, read back by psc_synchronize.
 constexpr int32_t kErrListOverflow = 1;
 constexpr int32_t kErrBirthOverflow = 2;
+constexpr int32_t kErrClaimTableFull = 4;
 
 // n / d for n, d < 2^31 by one high multiply (round-up reciprocal).
 struct FastDiv {
@@ -88,11 +89,25 @@ struct Birth {
     uint64_t img;
 };
 
+// Where the claims of one event go.  Direct: one 32-bit word per voxel (small
+// lattices), reset by the winner.  Hash: open addressing over 64-bit slots
+// holding (voxel << 32 | lowest id); two tables alternate between events and
+// the commit kernel of one event empties the table of the previous one.
+struct ClaimTable {
+    uint32_t* direct;
+    uint64_t* hash;
+    uint32_t hash_bits;        // log2 of the slots in use this event
+    uint64_t* clear;           // table of the previous event (hash mode)
+    uint32_t clear_n;          // its slots to reset
+};
+constexpr uint64_t kEmptySlot = ~0ull;
+
 // Everything one event kernel needs, passed by value.
 struct EventArgs {
     Geometry geo;
-    uint16_t* occ;
-    uint32_t* claim;
+    uint16_t* occ;             // species codes (exact for species with reactions)
+    uint32_t* bits;            // vacancy mirror: bit v set = voxel v occupied
+    ClaimTable ct;
     SpeciesList list;          // list of the due species
     const int32_t* count;      // its length (device)
     const ModelDev* model;
@@ -102,11 +117,13 @@ struct EventArgs {
     uint32_t key0, key1;       // Philox key = seed
     uint32_t g;                // global event index
     int32_t s;                 // due species
+    int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;
 };
 
 struct ReconcileArgs {
     uint16_t* occ;
+    const uint32_t* bits;
     int32_t x;                 // species whose list is reconciled
     SpeciesList list;
     SpeciesList tmp;
@@ -118,6 +135,11 @@ struct ReconcileArgs {
 void upload_stencil(cudaStream_t st);
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
 void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
+void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st);
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V, int blocks,
+                        cudaStream_t st);
+void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
+                          int blocks, cudaStream_t st);
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
 void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
 void launch_births(const EventArgs& a, cudaStream_t st);
@@ -125,8 +147,8 @@ void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStre
 void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
                           int blocks, cudaStream_t st);
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, const ModelDev* model, int blocks,
-                             cudaStream_t st);
+                             int n_species, uint16_t* occ, uint32_t* bits, const ModelDev* model,
+                             int blocks, cudaStream_t st);
 void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st);
 void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32_t* perm,

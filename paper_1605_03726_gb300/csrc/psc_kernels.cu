@@ -5,15 +5,23 @@
 //   claim    every molecule draws (Philox), takes its first-order test, picks a
 //            neighbour, reads the grid as it was at the start of the event and,
 //            if the neighbour is vacant (or holds a partner and the collision is
-//            accepted), claims it with atomicMin of its id: the lowest id wins;
+//            accepted), claims it: the claim slot of a voxel keeps the lowest id;
 //   commit   each winner writes the grid (move, reaction products, first-order
-//            products) and resets its claim word, so the claim array is all
-//            kNoClaim again when the event ends;
+//            products);
 //   reconcile   (only for species touched by reactions) lists are brought back
 //            in line with the grid: an entry whose voxel now holds another
 //            species moves to that species' list, an emptied one is dropped;
 //   births   fresh ids for second first-order products, in parent-id order.
 // The hot path of a diffusion-only species is claim + commit.
+//
+// Grid state.  Vacancy lives in a 1-bit-per-voxel mirror (16.8 MB at 512^3, so
+// it stays in L2); the 16-bit species codes are kept exact for every species
+// that takes part in a reaction.  A species without reactions skips the code
+// writes while it moves: nothing reads its codes before a read-out, which
+// rebuilds them from its list.  Claims go to a per-voxel word on small
+// lattices and to a compact hash table (two slots per molecule) on large ones,
+// so the claim traffic of an event touches a few MB instead of random words
+// of a V-sized array.
 #include "psc_internal.h"
 
 namespace psc {
@@ -170,9 +178,85 @@ __device__ __forceinline__ void flush_stat(unsigned long long* dst, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
+// vacancy mirror and claim tables
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool occupied(const uint32_t* bits, uint32_t v)
+{
+    return (bits[v >> 5] >> (v & 31u)) & 1u;
+}
+
+__device__ __forceinline__ void bit_set(uint32_t* bits, uint32_t v)
+{
+    atomicOr(&bits[v >> 5], 1u << (v & 31u));
+}
+
+__device__ __forceinline__ void bit_clear(uint32_t* bits, uint32_t v)
+{
+    atomicAnd(&bits[v >> 5], ~(1u << (v & 31u)));
+}
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t hash_bits)
+{
+    return (t * 2654435761u) >> (32u - hash_bits);     // Fibonacci hashing
+}
+
+// Claim voxel t for molecule id: the slot for t ends up holding the lowest id.
+template <bool HASH>
+__device__ __forceinline__ void claim(const EventArgs& a, uint32_t t, uint32_t id)
+{
+    if (!HASH) {
+        atomicMin(&a.ct.direct[t], id);
+        return;
+    }
+    const uint32_t mask = (1u << a.ct.hash_bits) - 1u;
+    const uint64_t mine = ((uint64_t)t << 32) | id;
+    uint32_t h = slot_of(t, a.ct.hash_bits);
+    uint64_t cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        if (cur == kEmptySlot) {
+            const unsigned long long prev =
+                atomicCAS((unsigned long long*)&a.ct.hash[h], (unsigned long long)kEmptySlot,
+                          (unsigned long long)mine);
+            if (prev == kEmptySlot) return;
+            cur = prev;
+        }
+        if ((uint32_t)(cur >> 32) == t) {
+            // same voxel: the slot's key never changes within the event, so the
+            // 64-bit minimum is the minimum over ids
+            if ((uint32_t)cur > id) atomicMin((unsigned long long*)&a.ct.hash[h], (unsigned long long)mine);
+            return;
+        }
+        h = (h + 1u) & mask;
+        cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
+    }
+    atomicOr(&a.sc->err, kErrClaimTableFull);
+}
+
+// Did molecule id win voxel t?  (Direct mode: the winner resets the word, which
+// every loser then reads as "not mine".)
+template <bool HASH>
+__device__ __forceinline__ bool won(const EventArgs& a, uint32_t t, uint32_t id)
+{
+    if (!HASH) {
+        if (a.ct.direct[t] != id) return false;
+        a.ct.direct[t] = kNoClaim;
+        return true;
+    }
+    const uint32_t mask = (1u << a.ct.hash_bits) - 1u;
+    uint32_t h = slot_of(t, a.ct.hash_bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint64_t cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
+        if (cur == kEmptySlot) return false;
+        if ((uint32_t)(cur >> 32) == t) return (uint32_t)cur == id;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // claim
 // ---------------------------------------------------------------------------
-template <bool GENERAL>
+template <bool GENERAL, bool HASH>
 __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
 {
     const int32_t n = *a.count;
@@ -180,8 +264,6 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
     unsigned long long n_att = 0, n_col = 0, n_acc = 0, n_fire = 0;
     const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
     const int stride = gridDim.x * blockDim.x;
-    // the loop bound is uniform per warp, so the warp-level stat flush below
-    // sees all 32 lanes
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
@@ -202,14 +284,14 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
                     int c = 0;
                     for (int d = 0; d < 12; ++d) {
                         int32_t t; uint64_t w;
-                        if (neighbor(a.geo, i, j, k, d, t, w) && a.occ[t] == 0) ++c;
+                        if (neighbor(a.geo, i, j, k, d, t, w) && !occupied(a.bits, t)) ++c;
                     }
                     if (c > 0) {
                         int want = (int)__umulhi(u[0], (uint32_t)c);
                         for (int d = 0; d < 12; ++d) {
                             int32_t t; uint64_t w;
-                            if (neighbor(a.geo, i, j, k, d, t, w) && a.occ[t] == 0) {
-                                if (want == 0) { atomicMin(&a.claim[t], id); break; }
+                            if (neighbor(a.geo, i, j, k, d, t, w) && !occupied(a.bits, t)) {
+                                if (want == 0) { claim<HASH>(a, (uint32_t)t, id); break; }
                                 --want;
                             }
                         }
@@ -221,16 +303,18 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
         const int d = (int)__umulhi(u[0], 12u);
         int32_t t; uint64_t w;
         if (!neighbor(a.geo, i, j, k, d, t, w)) continue;
-        const uint16_t o = a.occ[t];
-        if (o == 0) {
-            atomicMin(&a.claim[t], id);
-        } else if (GENERAL && o != kBlocked) {
-            const int r = a.model->pair[a.s][o - 1];
-            if (r >= 0) {
-                ++n_col;
-                if ((uint64_t)u[1] < a.model->rx[r].T) {
-                    ++n_acc;
-                    atomicMin(&a.claim[t], id);
+        if (!occupied(a.bits, (uint32_t)t)) {
+            claim<HASH>(a, (uint32_t)t, id);
+        } else if (GENERAL) {
+            const uint16_t o = a.occ[t];
+            if (o != 0 && o != kBlocked) {
+                const int r = a.model->pair[a.s][o - 1];
+                if (r >= 0) {
+                    ++n_col;
+                    if ((uint64_t)u[1] < a.model->rx[r].T) {
+                        ++n_acc;
+                        claim<HASH>(a, (uint32_t)t, id);
+                    }
                 }
             }
         }
@@ -248,7 +332,7 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
 // ---------------------------------------------------------------------------
 // commit
 // ---------------------------------------------------------------------------
-template <bool GENERAL>
+template <bool GENERAL, bool HASH>
 __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
 {
     const int32_t n = *a.count;
@@ -256,6 +340,11 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
     const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
     const uint16_t self = (uint16_t)(a.s + 1);
     const int stride = gridDim.x * blockDim.x;
+    if (HASH) {
+        // empty the table of the previous event for the next one
+        for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < a.ct.clear_n; x += stride)
+            a.ct.clear[x] = kEmptySlot;
+    }
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
@@ -270,14 +359,14 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
             if (M->n_fo[a.s] > 0 && (uint64_t)u[2] < M->T_fire[a.s]) {
                 const ReactionDev R = M->rx[pick_first_order(M, a.s, u[3])];
                 if (R.np == 2) {
-                    // the claimed neighbour, if this molecule won it, still
-                    // carries its id: no other thread writes that word
+                    // the neighbour this molecule claimed, if it won it
                     for (int d = 0; d < 12; ++d) {
                         int32_t t; uint64_t w;
-                        if (!neighbor(a.geo, i, j, k, d, t, w) || a.claim[t] != id) continue;
-                        a.claim[t] = kNoClaim;
+                        if (!neighbor(a.geo, i, j, k, d, t, w) || occupied(a.bits, (uint32_t)t)) continue;
+                        if (!won<HASH>(a, (uint32_t)t, id)) continue;
                         a.occ[v] = (uint16_t)(R.p0 + 1);
                         a.occ[t] = (uint16_t)(R.p1 + 1);
+                        bit_set(a.bits, (uint32_t)t);
                         const int slot = atomicAdd(&a.sc->births, 1);
                         if (slot < a.births_cap) {
                             Birth b;
@@ -291,7 +380,12 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
                         break;
                     }
                 } else {
-                    a.occ[v] = R.np ? (uint16_t)(R.p0 + 1) : (uint16_t)0;
+                    if (R.np) {
+                        a.occ[v] = (uint16_t)(R.p0 + 1);
+                    } else {
+                        a.occ[v] = 0;
+                        bit_clear(a.bits, v);
+                    }
                     ++n_r1;
                 }
                 continue;
@@ -300,12 +394,16 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
         const int d = (int)__umulhi(u[0], 12u);
         int32_t t; uint64_t w;
         if (!neighbor(a.geo, i, j, k, d, t, w)) continue;
-        if (a.claim[t] != id) continue;            // lost, or never claimed
-        a.claim[t] = kNoClaim;
+        if (!won<HASH>(a, (uint32_t)t, id)) continue;       // lost, or never claimed
         const uint16_t o = GENERAL ? a.occ[t] : (uint16_t)0;
-        if (o == 0) {
-            a.occ[t] = self;
-            a.occ[v] = 0;
+        if (!GENERAL || !occupied(a.bits, (uint32_t)t)) {
+            // move (Sec. 2.3)
+            bit_clear(a.bits, v);
+            bit_set(a.bits, (uint32_t)t);
+            if (a.live) {
+                a.occ[t] = self;
+                a.occ[v] = 0;
+            }
             a.list.vox[idx] = t;
             if (w) a.list.img[idx] = img_add(a.list.img[idx], w);
             ++n_hop;
@@ -313,8 +411,18 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
             // accepted collision with partner o - 1 (Sec. 2.4.2): first
             // product on the partner's voxel, second on the mover's
             const ReactionDev R = a.model->rx[a.model->pair[a.s][o - 1]];
-            a.occ[t] = R.np >= 1 ? (uint16_t)(R.p0 + 1) : (uint16_t)0;
-            a.occ[v] = R.np == 2 ? (uint16_t)(R.p1 + 1) : (uint16_t)0;
+            if (R.np >= 1) {
+                a.occ[t] = (uint16_t)(R.p0 + 1);
+            } else {
+                a.occ[t] = 0;
+                bit_clear(a.bits, (uint32_t)t);
+            }
+            if (R.np == 2) {
+                a.occ[v] = (uint16_t)(R.p1 + 1);
+            } else {
+                a.occ[v] = 0;
+                bit_clear(a.bits, v);
+            }
             ++n_r2;
         }
     }
@@ -329,21 +437,35 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
 
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)
 {
-    if (general) k_claim<true><<<blocks, threads, 0, st>>>(a);
-    else k_claim<false><<<blocks, threads, 0, st>>>(a);
+    const bool hash = a.ct.hash != nullptr;
+    if (general) {
+        if (hash) k_claim<true, true><<<blocks, threads, 0, st>>>(a);
+        else k_claim<true, false><<<blocks, threads, 0, st>>>(a);
+    } else {
+        if (hash) k_claim<false, true><<<blocks, threads, 0, st>>>(a);
+        else k_claim<false, false><<<blocks, threads, 0, st>>>(a);
+    }
 }
 
 void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)
 {
-    if (general) k_commit<true><<<blocks, threads, 0, st>>>(a);
-    else k_commit<false><<<blocks, threads, 0, st>>>(a);
+    const bool hash = a.ct.hash != nullptr;
+    if (general) {
+        if (hash) k_commit<true, true><<<blocks, threads, 0, st>>>(a);
+        else k_commit<true, false><<<blocks, threads, 0, st>>>(a);
+    } else {
+        if (hash) k_commit<false, true><<<blocks, threads, 0, st>>>(a);
+        else k_commit<false, false><<<blocks, threads, 0, st>>>(a);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // reconcile: bring the list of species x in line with the grid after an event
 // with reactions.  An entry whose voxel holds x stays; one whose voxel holds
 // species y (a product that inherited this molecule's identity) moves to y's
-// list; one whose voxel is empty is dropped.
+// list; one whose voxel is empty is dropped.  Species with reactions always
+// keep their codes in occ, and a vacant voxel never keeps the code of one, so
+// "occupied and code y + 1" identifies y exactly.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int warp_alloc(int* counter, bool want)
 {
@@ -370,7 +492,7 @@ __global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
             v = r.list.vox[idx];
             id = r.list.ids[idx];
             img = r.list.img[idx];
-            o = r.occ[v];
+            o = ((r.bits[(uint32_t)v >> 5] >> ((uint32_t)v & 31u)) & 1u) ? r.occ[v] : (uint16_t)0;
         }
         const bool keep = valid && o == self;
         const int slot = warp_alloc(&r.sc->tmp_count[r.x], keep);
@@ -494,6 +616,45 @@ void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStre
     k_fill_u32<<<blocks, 256, 0, st>>>(p, value, n);
 }
 
+__global__ void k_fill_u64(uint64_t* p, uint64_t value, size_t n)
+{
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x)
+        p[x] = value;
+}
+
+void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st)
+{
+    k_fill_u64<<<blocks, 256, 0, st>>>(p, value, n);
+}
+
+// exact species grid for read-out: the codes of species with reactions where
+// the mirror says occupied, zero elsewhere; species without reactions are
+// written afterwards from their lists (they do not keep codes while moving)
+__global__ void k_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = ((bits[v >> 5] >> (v & 31)) & 1u) ? occ[v] : (uint16_t)0;
+}
+
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V, int blocks,
+                        cudaStream_t st)
+{
+    k_materialize<<<blocks, 256, 0, st>>>(out, occ, bits, V);
+}
+
+__global__ void k_scatter_codes(uint16_t* out, const SpeciesList L, const int32_t* count, uint16_t code)
+{
+    const int32_t n = *count;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        out[L.vox[x]] = code;
+}
+
+void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
+                          int blocks, cudaStream_t st)
+{
+    k_scatter_codes<<<blocks, 256, 0, st>>>(out, list, count, code);
+}
+
 // placement key of every voxel: word 0 of Philox(seed; v, 0, 1, 0)
 __global__ void k_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1)
 {
@@ -517,7 +678,7 @@ struct Offsets {
 
 // rank r of the sorted voxels goes to the species whose range holds r
 __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, Offsets o, int n_species,
-                                   uint16_t* occ, const ModelDev* model)
+                                   uint16_t* occ, uint32_t* bits, const ModelDev* model)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_total;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -526,6 +687,7 @@ __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, 
         const uint32_t v = sorted_vox[r];
         const int64_t a = r - o.off[s];
         occ[v] = (uint16_t)(s + 1);
+        atomicOr(&bits[v >> 5], 1u << (v & 31u));
         const SpeciesList L = model->lists[s];
         L.vox[a] = (int32_t)v;
         L.ids[a] = (uint32_t)r;
@@ -534,12 +696,12 @@ __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, 
 }
 
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, const ModelDev* model, int blocks,
-                             cudaStream_t st)
+                             int n_species, uint16_t* occ, uint32_t* bits, const ModelDev* model,
+                             int blocks, cudaStream_t st)
 {
     Offsets o;
     for (int s = 0; s <= kMaxSpecies; ++s) o.off[s] = s <= n_species ? offsets[s] : offsets[n_species];
-    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, n_species, occ, model);
+    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, n_species, occ, bits, model);
 }
 
 // Morton (Z-order) key of the voxel of each list entry, 10 bits per axis

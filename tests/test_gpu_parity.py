@@ -54,7 +54,8 @@ def build_both(shape, recipe, seed, boundary=psc.PERIODIC_ALL, rv=1e-8, **opts):
 def test_ab_to_c_64cubed_full_run(seed):
     # 64^3 periodic, r_v 10 nm, A and B 2000 each (D 1 um^2/s), A + B -> C with
     # k = 1e-19 m^3/s, C immobile; run to 1000 hop intervals of A
-    g, o = build_both((64, 64, 64), lambda L: models.reaction_diffusion_ab(L, 2000, 2000), seed)
+    g, o = build_both((64, 64, 64), lambda L: models.reaction_diffusion_ab(L, 2000, 2000), seed,
+                      claim_table=1 + seed % 2)
     tau = g.tau(0)
     assert tau == o.tau(0)
     assert g.p_ab(0) == o.p_ab(0)
@@ -64,21 +65,24 @@ def test_ab_to_c_64cubed_full_run(seed):
         assert_same(g, o, "t=%d tau" % t)
 
 
+@pytest.mark.parametrize("claim_table", [1, 2])
 @pytest.mark.parametrize("shape,frac", [((96, 80, 64), 0.01), ((37, 24, 18), 0.30), ((50, 44, 30), 0.60)])
-def test_diffusion_ragged_shapes(shape, frac):
+def test_diffusion_ragged_shapes(shape, frac, claim_table):
     V = shape[0] * shape[1] * shape[2]
-    g, o = build_both(shape, lambda L: models.diffusion_only(L, int(frac * V)), 11, resort_period=7)
+    g, o = build_both(shape, lambda L: models.diffusion_only(L, int(frac * V)), 11, resort_period=7,
+                      claim_table=claim_table)
     for _ in range(4):
         g.run_events(13)
         o.run_events(13)
         assert_same(g, o)
 
 
-def test_reflective_crowded_reversible():
+@pytest.mark.parametrize("claim_table", [1, 2])
+def test_reflective_crowded_reversible(claim_table):
     shape = (40, 36, 32)
     V = 40 * 36 * 32
     g, o = build_both(shape, lambda L: models.crowded_reversible(L, V, kb=2000.0), 5, boundary=0,
-                      collect_stats=1)
+                      collect_stats=1, claim_table=claim_table)
     for _ in range(5):
         g.run_events(60)
         o.run_events(60)
@@ -89,10 +93,11 @@ def test_reflective_crowded_reversible():
     assert so["reactions2"] > 0 and so["births"] > 0
 
 
-def test_mapk_like_cascade():
+@pytest.mark.parametrize("claim_table", [1, 2])
+def test_mapk_like_cascade(claim_table):
     shape = (40, 40, 40)
     recipe = lambda L: models.mapk_like(L, 7, scale=0.3, uni_scale=300, bi_scale=3)
-    g, o = build_both(shape, recipe, 7, collect_stats=1)
+    g, o = build_both(shape, recipe, 7, collect_stats=1, claim_table=claim_table)
     for _ in range(6):
         g.run_events(500)
         o.run_events(500)
@@ -102,33 +107,56 @@ def test_mapk_like_cascade():
     assert g.stats()["births"] == so["births"]
 
 
+@pytest.mark.parametrize("claim_table", [1, 2])
 @pytest.mark.parametrize("products", [[], [2], [2, 3]])
-def test_second_order_product_counts(products):
+def test_second_order_product_counts(products, claim_table):
     def recipe(L):
         a = L.add_species(2e-12, 1500)
         b = L.add_species(1e-12, 1500)
         L.add_species(0.5e-12, 0)
         L.add_species(0.0, 0)
         L.add_reaction([a, b], products, 5e-19)
-    g, o = build_both((32, 32, 32), recipe, 9)
+    g, o = build_both((32, 32, 32), recipe, 9, claim_table=claim_table)
     for _ in range(3):
         g.run_events(40)
         o.run_events(40)
         assert_same(g, o)
 
 
+@pytest.mark.parametrize("claim_table", [1, 2])
 @pytest.mark.parametrize("products", [[], [1], [1, 2], [0, 2]])
-def test_first_order_product_counts(products):
+def test_first_order_product_counts(products, claim_table):
     def recipe(L):
         a = L.add_species(1e-12, 3000)
         L.add_species(0.3e-12, 0)
         L.add_species(0.0, 0)
         L.add_reaction([a], products, 3000.0)
-    g, o = build_both((24, 24, 24), recipe, 4)
+    g, o = build_both((24, 24, 24), recipe, 4, claim_table=claim_table)
     for _ in range(3):
         g.run_events(25)
         o.run_events(25)
         assert_same(g, o)
+
+
+@pytest.mark.parametrize("claim_table", [1, 2])
+def test_walkers_without_reactions_among_reacting_species(claim_table):
+    # T moves but takes part in no reaction, so it keeps no codes in the grid
+    # while moving; A + B -> C + D and C -> A + B react around it
+    def recipe(L):
+        t = L.add_species(3e-12, 4000)
+        a = L.add_species(1e-12, 2500)
+        b = L.add_species(2e-12, 2500)
+        c = L.add_species(0.5e-12, 0)
+        d = L.add_species(1.5e-12, 0)
+        L.add_species(0.0, 3000)                   # immobile crowders, no reactions
+        L.add_reaction([a, b], [c, d], 4e-19)
+        L.add_reaction([c], [a, b], 5000.0)
+    g, o = build_both((36, 40, 30), recipe, 13, claim_table=claim_table, collect_stats=1)
+    for _ in range(6):
+        g.run_events(40)
+        o.run_events(40)
+        assert_same(g, o)
+    assert o.stats()["reactions2"] > 0
 
 
 def test_edge_cases():
@@ -188,7 +216,7 @@ def test_diffusion_512cubed_full_size():
     # the 512^3 lattice at 1 % occupancy (1,342,177 molecules, D = 10 um^2/s) in
     # the launch configuration the benchmark times
     n = int(0.01 * 512 ** 3)
-    g, o = build_both((512, 512, 512), lambda L: models.diffusion_only(L, n, D=10e-12), 1)
+    g, o = build_both((512, 512, 512), lambda L: models.diffusion_only(L, n, D=10e-12), 1, resort_period=100)
     g.run_events(3)
     o.run_events(3)
     assert_same(g, o)

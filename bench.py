@@ -133,13 +133,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_per_attempt():
-    """DRAM bytes per hop attempt of the claim + commit pair from the committed
-    ncu summary, or None (the file is written after each profile of the kernels)."""
-    p = os.path.join(ROOT, "profiles", "hop_step_512cubed_traffic.json")
+def profiled_traffic():
+    """DRAM bytes of one k_hop_run launch from the committed ncu summary
+    (profiles/hop_run_512cubed_traffic.txt), with the kernel revision it was
+    taken on; None if absent."""
+    p = os.path.join(ROOT, "profiles", "hop_run_512cubed_traffic.txt")
     try:
+        d = {}
         with open(p) as f:
-            d = json.load(f)
+            for line in f:
+                line = line.split("#", 1)[0].strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    d[k.strip()] = v.strip()
         return d
     except Exception:
         return None
@@ -214,27 +220,35 @@ def gpu_arm(args, rank, world, local):
     L.set_options(collect_stats=-1)
     s_frac = (st1["hops"] - st0["hops"]) / max(1, st1["attempts"] - st0["attempts"])
 
-    # roofline of the hop step: claim + commit kernels of one event
+    # roofline of the hop step: the persistent stretch kernel (claim and commit
+    # phases of every event), or claim + commit launches when it is off
     hbm, peak_kind = peaks()
     b_alg = 14.0 + 8.0 * s_frac            # bytes per attempt
-    n_ev = max(1, kt["claim_launches"])
-    t_event_ms = (kt["claim_ms"] + kt["commit_ms"]) / n_ev
+    persistent = kt["run_events"] > 0
+    n_ev = max(1, kt["claim_launches"] + kt["run_events"])
+    hop_ms = kt["claim_ms"] + kt["commit_ms"] + kt["run_ms"]
+    t_event_ms = hop_ms / n_ev
     achieved = b_alg * N_MOL / (t_event_ms * 1e-3) / 1e9
-    tr = traffic_per_attempt()
+    tr = profiled_traffic()
     traffic = None
-    if tr and tr.get("kernel_rev") == kernel_revision():
-        traffic = tr["bytes_per_event"]
+    events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
+    if persistent and tr and tr.get("kernel_rev") == kernel_revision() and \
+            int(tr.get("events_per_launch", 0)) == round(events_per_launch):
+        traffic = int(tr["dram_read_bytes"]) + int(tr["dram_write_bytes"])
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
         "frac": round(achieved / hbm, 4), "traffic": traffic,
-        "kernel": "k_claim + k_commit (one hop event over all molecules)",
+        "traffic_unit": "DRAM bytes per launch (ncu, profiles/hop_run_512cubed.md)",
+        "events_per_launch": events_per_launch,
+        "bytes_alg_per_launch": round(b_alg * N_MOL * events_per_launch),
+        "kernel": ("k_hop_run (persistent: claim phase, grid barrier, commit phase per event)" if persistent
+                   else "k_claim + k_commit (one hop event over all molecules)"),
         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
         "bytes_alg_per_attempt": round(b_alg, 3), "hop_success": round(s_frac, 5),
         "event_us": round(t_event_ms * 1e3, 3),
-        "claim_us": round(kt["claim_ms"] / n_ev * 1e3, 3),
-        "commit_us": round(kt["commit_ms"] / n_ev * 1e3, 3),
+        "launches_per_event": round((kt["claim_launches"] + kt["commit_launches"] + kt["run_launches"]) / n_ev, 4),
         "resort_us": round(kt["resort_ms"] / max(1, kt["resorts"]) * 1e3, 3),
-        "share_of_step": round((kt["claim_ms"] + kt["commit_ms"]) / max(1e-9, elapsed_ms), 4),
+        "share_of_step": round(hop_ms / max(1e-9, elapsed_ms), 4),
     }
     L.close()
     res = {"value": value, "elapsed_ms": elapsed_ms, "roofline": roofline, "clocks": clocks,

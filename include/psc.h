@@ -106,6 +106,8 @@ typedef struct {
 typedef struct {
     double claim_ms, commit_ms, reconcile_ms, resort_ms;
     int64_t claim_launches, commit_launches, reconcile_events, resorts;
+    double run_ms;            /* persistent launches over stretches of events  */
+    int64_t run_launches, run_events;
 } psc_kernel_times;
 
 /* Tunables; zero in a field keeps the current value. */
@@ -121,6 +123,15 @@ typedef struct {
                                  every event (psc_kernel_times_get), -1 off     */
     int32_t claim_table;      /* before populate: 1 = one claim word per voxel,
                                  2 = hash table of claims, 0/-1 = by size      */
+    int32_t persistent;       /* 1 = run stretches of events of a species without
+                                 reactions in one cooperative launch (default),
+                                 -1 = one claim + commit launch per event       */
+    int32_t slot_map;         /* home slot of a claim in the hash table:
+                                 1 = hashed voxel index (default), 2 = Morton
+                                 order, 3 = Morton with permuted low bits      */
+    int32_t claim_slots;      /* before populate: hash slots per molecule of
+                                 the largest mobile species, rounded up to a
+                                 power of two (default 3)                      */
 } psc_options;
 
 /*

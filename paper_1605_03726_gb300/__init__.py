@@ -34,14 +34,15 @@ class Stats(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
-        "claim_table")]
+        "claim_table", "persistent", "slot_map", "claim_slots")]
 
 
 class KernelTimes(ctypes.Structure):
     _fields_ = [("claim_ms", ctypes.c_double), ("commit_ms", ctypes.c_double),
                 ("reconcile_ms", ctypes.c_double), ("resort_ms", ctypes.c_double),
                 ("claim_launches", ctypes.c_int64), ("commit_launches", ctypes.c_int64),
-                ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64)]
+                ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64),
+                ("run_ms", ctypes.c_double), ("run_launches", ctypes.c_int64), ("run_events", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))

@@ -92,6 +92,7 @@ struct psc_lattice {
     uint64_t* tables[2] = {nullptr, nullptr};   // claim hash tables (large lattices)
     uint32_t table_used[2] = {0, 0};   // slots written by the event that used it
     int64_t table_slots = 0;
+    BarrierState* barrier = nullptr;
     uint32_t hash_bits[kMaxSpecies] = {};
     Scalars* sc = nullptr;
     Birth* births = nullptr;
@@ -109,13 +110,13 @@ struct psc_lattice {
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 0, 0, 0};
+    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3};
     int64_t launches = 0;
     uint64_t events = 0;
     uint64_t h2d = 0, d2h = 0;
 
     // CUDA-event spans around kernels (psc_options.time_kernels)
-    struct Span { cudaEvent_t a, b; int kind; };
+    struct Span { cudaEvent_t a, b; int kind; int64_t events; };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> event_pool;
     int sticky = PSC_OK;
@@ -177,6 +178,7 @@ EventArgs event_args(const psc_lattice* L, int s)
 {
     EventArgs a{};
     a.geo = L->geo;
+    a.geo.slot_map = (uint32_t)(L->opt.slot_map - 1);
     a.occ = L->occ;
     a.bits = L->bits;
     a.ct.direct = L->claim;
@@ -202,7 +204,7 @@ EventArgs event_args(const psc_lattice* L, int s)
     return a;
 }
 
-enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort };
+enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort, kSpanRun };
 
 cudaEvent_t take_event(psc_lattice* L)
 {
@@ -225,13 +227,13 @@ cudaEvent_t span_open(psc_lattice* L)
     return a;
 }
 
-void span_close(psc_lattice* L, cudaEvent_t a, int kind)
+void span_close(psc_lattice* L, cudaEvent_t a, int kind, int64_t events = 1)
 {
     if (!a) return;
     cudaEvent_t b = take_event(L);
     if (!b) { L->event_pool.push_back(a); return; }
     cudaEventRecord(b, L->stream);
-    L->spans.push_back({a, b, kind});
+    L->spans.push_back({a, b, kind, events});
 }
 
 int resort(psc_lattice* L, int s)
@@ -240,8 +242,8 @@ int resort(psc_lattice* L, int s)
     const SpeciesList& list = L->model_h.lists[s];
     const int32_t* count = &L->sc->counts[s];
     launch_morton_keys(list, count, L->geo, L->rs_keys, L->rs_vals, blocks, L->stream);
-    if (radix_sort_pairs(L->rs_keys, L->rs_vals, count, 0, L->cap[s], 30, L->rs_scratch, L->stream,
-                         &L->launches) != 0)
+    if (radix_sort_pairs(L->rs_keys, L->rs_vals, count, 0, L->cap[s], (int)morton_sort_bits(L->geo),
+                         L->rs_scratch, L->stream, &L->launches) != 0)
         return cuda_fail(L, cudaErrorUnknown);
     launch_permute(list, L->tmp, L->rs_vals, count, blocks, L->stream);
     launch_copy_list(L->tmp, list, count, blocks, L->stream);
@@ -269,6 +271,7 @@ int enqueue_event(psc_lattice* L, int s)
     sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
     for (int x : L->reconcile[s]) {
         ReconcileArgs r{};
+        r.geo = L->geo;
         r.occ = L->occ;
         r.bits = L->bits;
         r.x = x;
@@ -295,6 +298,42 @@ int enqueue_event(psc_lattice* L, int s)
         if (rc) return rc;
     }
     return cuda_fail(L, cudaPeekAtLastError());
+}
+
+// Can a stretch of events of species s run in one persistent launch?
+int run_width(const psc_lattice* L, int s, int* threads, int* blocks)
+{
+    if (L->opt.persistent <= 0 || L->general[s]) return 0;
+    if (L->tables[0] && L->hash_bits[s] > 27) return 0;
+    return run_capacity(L->cap[s], threads, blocks, L->sm_count);
+}
+
+int enqueue_run(psc_lattice* L, int s, int n_events, int per_thread, int threads, int blocks)
+{
+    cudaStream_t st = L->stream;
+    // both claim tables must start empty
+    for (int t = 0; t < 2; ++t) {
+        if (L->tables[t] && L->table_used[t]) {
+            launch_fill_u64(L->tables[t], kEmptySlot, L->table_used[t], L->sm_count * 4, st);
+            L->table_used[t] = 0;
+            L->launches += 1;
+        }
+    }
+    RunArgs r{};
+    r.ev = event_args(L, s);
+    r.tables[0] = L->tables[0];
+    r.tables[1] = L->tables[1];
+    r.n_events = n_events;
+    r.barrier = L->barrier;
+    int rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st));
+    if (rc) return rc;
+    cudaEvent_t sp = span_open(L);
+    rc = cuda_fail(L, launch_run(r, blocks, threads, per_thread, st));
+    span_close(L, sp, kSpanRun, n_events);
+    if (rc) return rc;
+    L->launches += 1;
+    L->events += (uint64_t)n_events;
+    return PSC_OK;
 }
 
 // Sec. 2.2: the next event belongs to the mobile species whose next diffusion
@@ -397,6 +436,8 @@ int psc_lattice_create(psc_lattice** out, int32_t ni, int32_t nj, int32_t nk, do
     L->geo.ninj = (uint32_t)ni * (uint32_t)nj;
     L->geo.div_ni = make_fastdiv((uint32_t)ni);
     L->geo.div_ninj = make_fastdiv(L->geo.ninj);
+    L->geo.nbi = (uint32_t)((ni + 3) / 4);
+    L->geo.nbj = (uint32_t)((nj + 3) / 4);
     *out = L;
     return PSC_OK;
 }
@@ -549,18 +590,30 @@ int psc_populate(psc_lattice* L, uint64_t seed)
 
     // ---- device memory ----
     const size_t V = (size_t)L->V;
-    const size_t nwords = ((size_t)L->V + 31) / 32;
+    const size_t nwords = (size_t)mirror_words(L->ni, L->nj, L->nk);
     L->occ = (uint16_t*)dev_alloc(L, V * sizeof(uint16_t));
     L->bits = (uint32_t*)dev_alloc(L, nwords * sizeof(uint32_t));
     L->sc = (Scalars*)dev_alloc(L, sizeof(Scalars));
     L->model_d = (ModelDev*)dev_alloc(L, sizeof(ModelDev));
-    if (!L->occ || !L->bits || !L->sc || !L->model_d) return PSC_E_NOMEM;
+    L->barrier = (BarrierState*)dev_alloc(L, sizeof(BarrierState));
+    uint32_t* mort = (uint32_t*)dev_alloc(L, (size_t)(L->ni + L->nj + L->nk) * sizeof(uint32_t));
+    if (!L->occ || !L->bits || !L->sc || !L->model_d || !L->barrier || !mort) return PSC_E_NOMEM;
+    {
+        std::vector<uint32_t> mt((size_t)(L->ni + L->nj + L->nk));
+        uint32_t mbits = 0;
+        build_morton_tables(L->ni, L->nj, L->nk, mt.data(), &mbits);
+        int rc0 = cuda_fail(L, cudaMemcpy(mort, mt.data(), mt.size() * 4, cudaMemcpyHostToDevice));
+        if (rc0) return rc0;
+        L->h2d += mt.size() * 4;
+        L->geo.mort = mort;
+        L->geo.mort_bits = mbits;
+    }
     // claims: a word per voxel on small lattices, else two hash tables with at
     // least two slots per molecule of the largest mobile species
     uint32_t hb_max = 0;
     for (int s = 0; s < L->nsp; ++s) {
         uint32_t hb = 10;
-        while (hb < 31 && (1ll << hb) < 2ll * L->cap[s]) ++hb;
+        while (hb < 31 && (1ll << hb) < (int64_t)L->opt.claim_slots * L->cap[s]) ++hb;
         L->hash_bits[s] = hb;
         if (L->sp[s].D > 0.0 && hb > hb_max) hb_max = hb;
     }
@@ -630,7 +683,7 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         int64_t off[kMaxSpecies + 1];
         off[0] = 0;
         for (int s = 0; s < L->nsp; ++s) off[s + 1] = off[s] + L->sp[s].n0;
-        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->bits, L->model_d, fill_blocks, st);
+        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->bits, L->geo, L->model_d, fill_blocks, st);
         if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
         dev_free_one(L, keys);
         dev_free_one(L, vals);
@@ -643,23 +696,71 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     return L->clamped ? PSC_W_PCLAMP : PSC_OK;
 }
 
+// Queue events in scheduler order until max_events are queued or the next
+// event lies after t_end.  Consecutive events of one species without
+// reactions are grouped into persistent stretches (cut at re-sort points).
+static int drive(psc_lattice* L, double t_end, int64_t max_events)
+{
+    int64_t queued = 0;
+    while (queued < max_events) {
+        int s;
+        double t;
+        if (!next_event(L, &s, &t) || t > t_end) break;
+        if (L->g == UINT32_MAX) return PSC_E_LIMIT;
+        int threads = 0, blocks = 0;
+        const int per = run_width(L, s, &threads, &blocks);
+        if (per > 0) {
+            // how long does species s stay next?
+            const uint32_t g0 = L->g;
+            int64_t limit = max_events - queued;
+            if (L->opt.resort_period > 0)
+                limit = std::min<int64_t>(limit, (int64_t)L->opt.resort_period - (int64_t)L->since_resort[s]);
+            limit = std::max<int64_t>(1, std::min<int64_t>(limit, (int64_t)UINT32_MAX - L->g));
+            int64_t e = 0;
+            for (;;) {
+                L->sp[s].done++;
+                L->g++;
+                L->clock = t;
+                ++e;
+                if (e >= limit) break;
+                int s2;
+                double t2;
+                if (!next_event(L, &s2, &t2) || s2 != s || t2 > t_end) break;
+                t = t2;
+            }
+            L->g = g0;                                   // event_args reads the first index
+            int rc = enqueue_run(L, s, (int)e, per, threads, blocks);
+            L->g = g0 + (uint32_t)e;
+            if (rc) return rc;
+            queued += e;
+            L->since_resort[s] += (uint64_t)e;
+            if (L->opt.resort_period > 0 && L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
+                L->since_resort[s] = 0;
+                cudaEvent_t sp = span_open(L);
+                rc = resort(L, s);
+                span_close(L, sp, kSpanResort);
+                if (rc) return rc;
+            }
+            continue;
+        }
+        int rc = enqueue_event(L, s);
+        if (rc) return rc;
+        L->sp[s].done++;
+        L->g++;
+        L->clock = t;
+        ++queued;
+    }
+    return PSC_OK;
+}
+
 int psc_run(psc_lattice* L, double t_end)
 {
     if (!L || !std::isfinite(t_end)) return PSC_E_ARG;
     if (!L->populated) return PSC_E_ORDER;
     if (L->sticky) return L->sticky;
     DevGuard dg(L->device);
-    for (;;) {
-        int s;
-        double t;
-        if (!next_event(L, &s, &t) || t > t_end) break;
-        if (L->g == UINT32_MAX) return PSC_E_LIMIT;
-        int rc = enqueue_event(L, s);
-        if (rc) return rc;
-        L->sp[s].done++;
-        L->g++;
-        L->clock = t;
-    }
+    int rc = drive(L, t_end, INT64_MAX);
+    if (rc) return rc;
     if (t_end > L->clock) L->clock = t_end;
     return PSC_OK;
 }
@@ -670,18 +771,7 @@ int psc_run_events(psc_lattice* L, int64_t n_events)
     if (!L->populated) return PSC_E_ORDER;
     if (L->sticky) return L->sticky;
     DevGuard dg(L->device);
-    for (int64_t e = 0; e < n_events; ++e) {
-        int s;
-        double t;
-        if (!next_event(L, &s, &t)) break;
-        if (L->g == UINT32_MAX) return PSC_E_LIMIT;
-        int rc = enqueue_event(L, s);
-        if (rc) return rc;
-        L->sp[s].done++;
-        L->g++;
-        L->clock = t;
-    }
-    return PSC_OK;
+    return drive(L, INFINITY, n_events);
 }
 
 int psc_synchronize(psc_lattice* L)
@@ -797,7 +887,7 @@ int psc_grid(psc_lattice* L, uint16_t* occ)
     uint16_t* tmp = (uint16_t*)dev_alloc(L, (size_t)L->V * 2);
     if (!tmp) return PSC_E_NOMEM;
     const int blocks = L->sm_count * 8;
-    launch_materialize(tmp, L->occ, L->bits, L->V, blocks, L->stream);
+    launch_materialize(tmp, L->occ, L->bits, L->geo, L->V, blocks, L->stream);
     for (int s = 0; s < L->nsp; ++s)
         if (!L->live[s])
             launch_scatter_codes(tmp, L->model_h.lists[s], &L->sc->counts[s], (uint16_t)(s + 1), blocks,
@@ -867,6 +957,16 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
         if (L->populated) return PSC_E_ORDER;
         L->opt.claim_table = o->claim_table;
     }
+    if (o->persistent) L->opt.persistent = o->persistent;
+    if (o->slot_map) {
+        if (o->slot_map < 1 || o->slot_map > 3) return PSC_E_ARG;
+        L->opt.slot_map = o->slot_map;
+    }
+    if (o->claim_slots) {
+        if (o->claim_slots < 2 || o->claim_slots > 64) return PSC_E_ARG;
+        if (L->populated) return PSC_E_ORDER;
+        L->opt.claim_slots = o->claim_slots;
+    }
     return PSC_OK;
 }
 
@@ -884,6 +984,7 @@ int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
         case kSpanClaim: out->claim_ms += ms; out->claim_launches++; break;
         case kSpanCommit: out->commit_ms += ms; out->commit_launches++; break;
         case kSpanReconcile: out->reconcile_ms += ms; out->reconcile_events++; break;
+        case kSpanRun: out->run_ms += ms; out->run_launches++; out->run_events += sp.events; break;
         default: out->resort_ms += ms; out->resorts++; break;
         }
         L->event_pool.push_back(sp.a);
@@ -896,7 +997,8 @@ int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
 int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
 {
     if (!L || !bytes) return PSC_E_ARG;
-    int64_t b = L->V * 2 + (L->V + 31) / 32 * 4 + (int64_t)sizeof(Scalars) + (int64_t)sizeof(ModelDev);
+    int64_t b = L->V * 2 + (int64_t)mirror_words(L->ni, L->nj, L->nk) * 4 + (int64_t)sizeof(Scalars) +
+                (int64_t)sizeof(ModelDev);
     if (L->claim) b += L->V * 4;
     b += 2 * L->table_slots * 8;
     int64_t N = 0;

@@ -22,6 +22,14 @@ constexpr uint32_t kTagPopulate = 1u;
 constexpr int32_t kErrListOverflow = 1;
 constexpr int32_t kErrBirthOverflow = 2;
 constexpr int32_t kErrClaimTableFull = 4;
+constexpr int32_t kErrBarrierTimeout = 8;
+
+// grid-wide barrier state of the persistent hop kernel: one arrival word whose
+// top bit flips each time every block has arrived
+struct BarrierState {
+    unsigned int arrive;
+    unsigned int pad;
+};
 
 // n / d for n, d < 2^31 by one high multiply (round-up reciprocal).
 struct FastDiv {
@@ -37,7 +45,22 @@ struct Geometry {
     uint32_t ninj;
     FastDiv div_ni;
     FastDiv div_ninj;
+    uint32_t nbi, nbj;    // vacancy-mirror bricks (4 x 4 x 2 voxels per word) along i, j
+    // compact Morton code of a voxel = mort[i] | mort[ni + j] | mort[ni + nj + k]
+    // (bits of the three axes interleaved, axes with fewer bits dropping out
+    // at the top), mort_bits wide
+    const uint32_t* mort;
+    uint32_t mort_bits;
+    uint32_t slot_map;    // claim-table home slot: 0 hashed voxel index, 1 Morton,
+                          // 2 Morton with the low 10 bits permuted
 };
+// host: spread tables of the compact Morton code (ni + nj + nk words)
+void build_morton_tables(int32_t ni, int32_t nj, int32_t nk, uint32_t* out, uint32_t* bits);
+// words of the vacancy mirror for an ni x nj x nk lattice
+inline uint64_t mirror_words(int32_t ni, int32_t nj, int32_t nk)
+{
+    return (uint64_t)((ni + 3) / 4) * (uint64_t)((nj + 3) / 4) * (uint64_t)((nk + 1) / 2);
+}
 
 // Structure-of-arrays list of the molecules of one species.  img packs three
 // 16-bit periodic wrap counters (i at bits 0-15, j at 16-31, k at 32-47).
@@ -121,7 +144,17 @@ struct EventArgs {
     int32_t collect_stats;
 };
 
+// A stretch of consecutive events of one species without reactions, run by
+// one persistent cooperative launch.
+struct RunArgs {
+    EventArgs ev;              // g = index of the first event
+    uint64_t* tables[2];       // claim tables, alternating by event parity
+    int32_t n_events;
+    BarrierState* barrier;
+};
+
 struct ReconcileArgs {
+    Geometry geo;
     uint16_t* occ;
     const uint32_t* bits;
     int32_t x;                 // species whose list is reconciled
@@ -136,8 +169,12 @@ void upload_stencil(cudaStream_t st);
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
 void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
 void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st);
-void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V, int blocks,
-                        cudaStream_t st);
+// Molecules per thread the persistent kernel holds in registers (0 = the
+// stretch does not fit); threads = its launch width.
+int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count);
+cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st);
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
+                        int64_t V, int blocks, cudaStream_t st);
 void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
                           int blocks, cudaStream_t st);
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
@@ -147,10 +184,11 @@ void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStre
 void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
                           int blocks, cudaStream_t st);
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, uint32_t* bits, const ModelDev* model,
-                             int blocks, cudaStream_t st);
+                             int n_species, uint16_t* occ, uint32_t* bits, const Geometry& geo,
+                             const ModelDev* model, int blocks, cudaStream_t st);
 void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st);
+uint32_t morton_sort_bits(const Geometry& geo);
 void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32_t* perm,
                     const int32_t* count, int blocks, cudaStream_t st);
 void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count,

@@ -24,6 +24,8 @@
 // of a V-sized array.
 #include "psc_internal.h"
 
+#include <algorithm>
+
 namespace psc {
 
 // HCP stencil in twisted Cartesian coordinates (Sec. 2.1): for directions
@@ -59,6 +61,36 @@ void upload_stencil(cudaStream_t st)
     h[2] = pack_offsets(dj0); h[3] = pack_offsets(dj1);
     h[4] = pack_offsets(dk);
     cudaMemcpyToSymbolAsync(c_stencil, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+}
+
+// Compact Morton code: level by level from the least significant bit, the
+// next bit of i, of j, of k in turn, skipping an axis once its extent is used
+// up; codes wider than 32 bits keep their top 32.
+void build_morton_tables(int32_t ni, int32_t nj, int32_t nk, uint32_t* out, uint32_t* bits_out)
+{
+    const int32_t n[3] = {ni, nj, nk};
+    int nb[3];
+    for (int a = 0; a < 3; ++a) {
+        nb[a] = 0;
+        while ((1ll << nb[a]) < n[a]) ++nb[a];
+    }
+    int pos[3][32];
+    int total = 0;
+    const int levels = std::max(nb[0], std::max(nb[1], nb[2]));
+    for (int l = 0; l < levels; ++l)
+        for (int a = 0; a < 3; ++a)
+            if (l < nb[a]) pos[a][l] = total++;
+    const int drop = total > 32 ? total - 32 : 0;
+    uint32_t* dst = out;
+    for (int a = 0; a < 3; ++a) {
+        for (int32_t x = 0; x < n[a]; ++x) {
+            uint64_t c = 0;
+            for (int l = 0; l < nb[a]; ++l)
+                if ((x >> l) & 1) c |= 1ull << pos[a][l];
+            *dst++ = (uint32_t)(c >> drop);
+        }
+    }
+    *bits_out = (uint32_t)(total - drop);
 }
 
 FastDiv make_fastdiv(uint32_t d)
@@ -110,10 +142,14 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
     u[0] = c0; u[1] = c1; u[2] = c2; u[3] = c3;
 }
 
+// neighbour of a voxel: linear index, coordinates, change of the wrap counters
+struct Nb {
+    int32_t t, i, j, k;
+    uint64_t wrap;
+};
+
 // Neighbour d of (i, j, k); false if it lies behind a reflective wall.
-// wrap receives the change of the packed 16-bit wrap counters.
-__device__ __forceinline__ bool neighbor(const Geometry& G, int32_t i, int32_t j, int32_t k, int d,
-                                         int32_t& t, uint64_t& wrap)
+__device__ __forceinline__ bool neighbor(const Geometry& G, int32_t i, int32_t j, int32_t k, int d, Nb& nb)
 {
     const uint32_t s0 = c_stencil[0], s1 = c_stencil[1], s2 = c_stencil[2], s3 = c_stencil[3],
                    s4 = c_stencil[4];
@@ -144,8 +180,9 @@ __device__ __forceinline__ bool neighbor(const Geometry& G, int32_t i, int32_t j
         if (!(G.bflags & 4u)) return false;
         tk -= G.nk; w |= 0x1ull << 32;
     }
-    t = ti + G.ni * (tj + G.nj * tk);
-    wrap = w;
+    nb.t = ti + G.ni * (tj + G.nj * tk);
+    nb.i = ti; nb.j = tj; nb.k = tk;
+    nb.wrap = w;
     return true;
 }
 
@@ -178,72 +215,120 @@ __device__ __forceinline__ void flush_stat(unsigned long long* dst, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
-// vacancy mirror and claim tables
+// vacancy mirror: one bit per voxel, words are 4 x 4 x 2 bricks (i, j, k) so a
+// hop often stays inside one word and flips both bits with one atomicXor
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool occupied(const uint32_t* bits, uint32_t v)
+struct BitPos {
+    uint32_t word, mask;
+};
+
+__device__ __forceinline__ BitPos bitpos(const Geometry& G, int32_t i, int32_t j, int32_t k)
 {
-    return (bits[v >> 5] >> (v & 31u)) & 1u;
+    BitPos b;
+    b.word = (((uint32_t)k >> 1) * G.nbj + ((uint32_t)j >> 2)) * G.nbi + ((uint32_t)i >> 2);
+    b.mask = 1u << (((uint32_t)i & 3u) | (((uint32_t)j & 3u) << 2) | (((uint32_t)k & 1u) << 4));
+    return b;
 }
 
-__device__ __forceinline__ void bit_set(uint32_t* bits, uint32_t v)
+__device__ __forceinline__ bool occupied(const uint32_t* bits, BitPos b)
 {
-    atomicOr(&bits[v >> 5], 1u << (v & 31u));
+    return (__ldcg(&bits[b.word]) & b.mask) != 0u;
 }
 
-__device__ __forceinline__ void bit_clear(uint32_t* bits, uint32_t v)
-{
-    atomicAnd(&bits[v >> 5], ~(1u << (v & 31u)));
-}
+__device__ __forceinline__ void bit_set(uint32_t* bits, BitPos b) { atomicOr(&bits[b.word], b.mask); }
+__device__ __forceinline__ void bit_clear(uint32_t* bits, BitPos b) { atomicAnd(&bits[b.word], ~b.mask); }
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t hash_bits)
+// a molecule leaves `from` (set) for `to` (clear)
+__device__ __forceinline__ void bit_move(uint32_t* bits, BitPos from, BitPos to)
 {
-    return (t * 2654435761u) >> (32u - hash_bits);     // Fibonacci hashing
-}
-
-// Claim voxel t for molecule id: the slot for t ends up holding the lowest id.
-template <bool HASH>
-__device__ __forceinline__ void claim(const EventArgs& a, uint32_t t, uint32_t id)
-{
-    if (!HASH) {
-        atomicMin(&a.ct.direct[t], id);
-        return;
+    if (from.word == to.word) {
+        atomicXor(&bits[from.word], from.mask | to.mask);
+    } else {
+        atomicAnd(&bits[from.word], ~from.mask);
+        atomicOr(&bits[to.word], to.mask);
     }
-    const uint32_t mask = (1u << a.ct.hash_bits) - 1u;
+}
+
+// ---------------------------------------------------------------------------
+// claim tables
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t morton(const Geometry& G, int32_t i, int32_t j, int32_t k)
+{
+    return __ldg(&G.mort[i]) | __ldg(&G.mort[G.ni + j]) | __ldg(&G.mort[G.ni + G.nj + k]);
+}
+
+// Home slot of voxel t = (i, j, k).  Map 0: Fibonacci hash of t (claims spread
+// over the whole table).  Map 1: the compact Morton code scaled to the table,
+// so molecules handled together (a stretch of the Morton-sorted list) claim a
+// compact region of it.  Map 2: as 1, with the low 10 bits permuted (odd
+// multiplier mod 1024) so neighbouring claims land on different cache lines.
+__device__ __forceinline__ uint32_t slot_of(const Geometry& G, uint32_t t, int32_t i, int32_t j, int32_t k,
+                                            uint32_t hash_bits)
+{
+    if (G.slot_map == 0u) return (t * 2654435761u) >> (32u - hash_bits);
+    const uint32_t c = morton(G, i, j, k);
+    uint32_t h = G.mort_bits >= hash_bits ? c >> (G.mort_bits - hash_bits) : c << (hash_bits - G.mort_bits);
+    if (G.slot_map == 2u && hash_bits > 10u) h = (h & ~0x3FFu) | ((h * 0x2C9u) & 0x3FFu);
+    return h;
+}
+
+// Claim voxel t = (i, j, k) for molecule id in an open-addressing table of
+// 2^hash_bits slots, starting at slot h whose content is believed to be cur;
+// the slot of t ends up holding the lowest id.  Returns the slot, or -1 if the
+// table is full (error raised).
+__device__ __forceinline__ int32_t hash_claim_from(uint64_t* tab, uint32_t hash_bits, uint32_t t, uint32_t id,
+                                                   uint32_t h, uint64_t cur, int32_t* err)
+{
+    const uint32_t mask = (1u << hash_bits) - 1u;
     const uint64_t mine = ((uint64_t)t << 32) | id;
-    uint32_t h = slot_of(t, a.ct.hash_bits);
-    uint64_t cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         if (cur == kEmptySlot) {
-            const unsigned long long prev =
-                atomicCAS((unsigned long long*)&a.ct.hash[h], (unsigned long long)kEmptySlot,
-                          (unsigned long long)mine);
-            if (prev == kEmptySlot) return;
+            const unsigned long long prev = atomicCAS((unsigned long long*)&tab[h],
+                                                      (unsigned long long)kEmptySlot, (unsigned long long)mine);
+            if (prev == kEmptySlot) return (int32_t)h;
             cur = prev;
         }
         if ((uint32_t)(cur >> 32) == t) {
-            // same voxel: the slot's key never changes within the event, so the
+            // same voxel: a slot's key never changes within the event, so the
             // 64-bit minimum is the minimum over ids
-            if ((uint32_t)cur > id) atomicMin((unsigned long long*)&a.ct.hash[h], (unsigned long long)mine);
-            return;
+            if ((uint32_t)cur > id) atomicMin((unsigned long long*)&tab[h], (unsigned long long)mine);
+            return (int32_t)h;
         }
         h = (h + 1u) & mask;
-        cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
+        cur = __ldcg((const unsigned long long*)&tab[h]);
     }
-    atomicOr(&a.sc->err, kErrClaimTableFull);
+    atomicOr(err, kErrClaimTableFull);
+    return -1;
 }
 
-// Did molecule id win voxel t?  (Direct mode: the winner resets the word, which
-// every loser then reads as "not mine".)
-template <bool HASH>
-__device__ __forceinline__ bool won(const EventArgs& a, uint32_t t, uint32_t id)
+__device__ __forceinline__ int32_t hash_claim(const Geometry& G, uint64_t* tab, uint32_t hash_bits, const Nb& nb,
+                                              uint32_t id, int32_t* err)
 {
+    const uint32_t h = slot_of(G, (uint32_t)nb.t, nb.i, nb.j, nb.k, hash_bits);
+    return hash_claim_from(tab, hash_bits, (uint32_t)nb.t, id, h,
+                           __ldcg((const unsigned long long*)&tab[h]), err);
+}
+
+template <bool HASH>
+__device__ __forceinline__ void claim(const EventArgs& a, const Nb& nb, uint32_t id)
+{
+    if (HASH) hash_claim(a.geo, a.ct.hash, a.ct.hash_bits, nb, id, &a.sc->err);
+    else atomicMin(&a.ct.direct[nb.t], id);
+}
+
+// Did molecule id win voxel nb?  (Direct mode: the winner resets the word,
+// which every loser then reads as "not mine".)
+template <bool HASH>
+__device__ __forceinline__ bool won(const EventArgs& a, const Nb& nb, uint32_t id)
+{
+    const uint32_t t = (uint32_t)nb.t;
     if (!HASH) {
         if (a.ct.direct[t] != id) return false;
         a.ct.direct[t] = kNoClaim;
         return true;
     }
     const uint32_t mask = (1u << a.ct.hash_bits) - 1u;
-    uint32_t h = slot_of(t, a.ct.hash_bits);
+    uint32_t h = slot_of(a.geo, t, nb.i, nb.j, nb.k, a.ct.hash_bits);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const uint64_t cur = __ldcg((const unsigned long long*)&a.ct.hash[h]);
         if (cur == kEmptySlot) return false;
@@ -283,15 +368,15 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
                     // second product: uniform pick among neighbours vacant now
                     int c = 0;
                     for (int d = 0; d < 12; ++d) {
-                        int32_t t; uint64_t w;
-                        if (neighbor(a.geo, i, j, k, d, t, w) && !occupied(a.bits, t)) ++c;
+                        Nb nb;
+                        if (neighbor(a.geo, i, j, k, d, nb) && !occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) ++c;
                     }
                     if (c > 0) {
                         int want = (int)__umulhi(u[0], (uint32_t)c);
                         for (int d = 0; d < 12; ++d) {
-                            int32_t t; uint64_t w;
-                            if (neighbor(a.geo, i, j, k, d, t, w) && !occupied(a.bits, t)) {
-                                if (want == 0) { claim<HASH>(a, (uint32_t)t, id); break; }
+                            Nb nb;
+                            if (neighbor(a.geo, i, j, k, d, nb) && !occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) {
+                                if (want == 0) { claim<HASH>(a, nb, id); break; }
                                 --want;
                             }
                         }
@@ -301,19 +386,19 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
             }
         }
         const int d = (int)__umulhi(u[0], 12u);
-        int32_t t; uint64_t w;
-        if (!neighbor(a.geo, i, j, k, d, t, w)) continue;
-        if (!occupied(a.bits, (uint32_t)t)) {
-            claim<HASH>(a, (uint32_t)t, id);
+        Nb nb;
+        if (!neighbor(a.geo, i, j, k, d, nb)) continue;
+        if (!occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) {
+            claim<HASH>(a, nb, id);
         } else if (GENERAL) {
-            const uint16_t o = a.occ[t];
+            const uint16_t o = a.occ[nb.t];
             if (o != 0 && o != kBlocked) {
                 const int r = a.model->pair[a.s][o - 1];
                 if (r >= 0) {
                     ++n_col;
                     if ((uint64_t)u[1] < a.model->rx[r].T) {
                         ++n_acc;
-                        claim<HASH>(a, (uint32_t)t, id);
+                        claim<HASH>(a, nb, id);
                     }
                 }
             }
@@ -352,6 +437,7 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
         const uint32_t id = a.list.ids[idx];
         int32_t i, j, k;
         decode(a.geo, v, i, j, k);
+        const BitPos bv = bitpos(a.geo, i, j, k);
         uint32_t u[4];
         philox(id, a.g, c2, 0u, a.key0, a.key1, u);
         if (GENERAL) {
@@ -359,19 +445,21 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
             if (M->n_fo[a.s] > 0 && (uint64_t)u[2] < M->T_fire[a.s]) {
                 const ReactionDev R = M->rx[pick_first_order(M, a.s, u[3])];
                 if (R.np == 2) {
-                    // the neighbour this molecule claimed, if it won it
+                    // the neighbour this molecule claimed, if it won it; only
+                    // its winner changes the bit of a claimed voxel
                     for (int d = 0; d < 12; ++d) {
-                        int32_t t; uint64_t w;
-                        if (!neighbor(a.geo, i, j, k, d, t, w) || occupied(a.bits, (uint32_t)t)) continue;
-                        if (!won<HASH>(a, (uint32_t)t, id)) continue;
+                        Nb nb;
+                        if (!neighbor(a.geo, i, j, k, d, nb)) continue;
+                        const BitPos bt = bitpos(a.geo, nb.i, nb.j, nb.k);
+                        if (occupied(a.bits, bt) || !won<HASH>(a, nb, id)) continue;
                         a.occ[v] = (uint16_t)(R.p0 + 1);
-                        a.occ[t] = (uint16_t)(R.p1 + 1);
-                        bit_set(a.bits, (uint32_t)t);
+                        a.occ[nb.t] = (uint16_t)(R.p1 + 1);
+                        bit_set(a.bits, bt);
                         const int slot = atomicAdd(&a.sc->births, 1);
                         if (slot < a.births_cap) {
                             Birth b;
-                            b.parent = id; b.t = t; b.species = R.p1; b.pad = 0;
-                            b.img = img_add(a.list.img[idx], w);
+                            b.parent = id; b.t = nb.t; b.species = R.p1; b.pad = 0;
+                            b.img = img_add(a.list.img[idx], nb.wrap);
                             a.births[slot] = b;
                         } else {
                             atomicOr(&a.sc->err, kErrBirthOverflow);
@@ -384,7 +472,7 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
                         a.occ[v] = (uint16_t)(R.p0 + 1);
                     } else {
                         a.occ[v] = 0;
-                        bit_clear(a.bits, v);
+                        bit_clear(a.bits, bv);
                     }
                     ++n_r1;
                 }
@@ -392,36 +480,37 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
             }
         }
         const int d = (int)__umulhi(u[0], 12u);
-        int32_t t; uint64_t w;
-        if (!neighbor(a.geo, i, j, k, d, t, w)) continue;
-        if (!won<HASH>(a, (uint32_t)t, id)) continue;       // lost, or never claimed
-        const uint16_t o = GENERAL ? a.occ[t] : (uint16_t)0;
-        if (!GENERAL || !occupied(a.bits, (uint32_t)t)) {
-            // move (Sec. 2.3)
-            bit_clear(a.bits, v);
-            bit_set(a.bits, (uint32_t)t);
+        Nb nb;
+        if (!neighbor(a.geo, i, j, k, d, nb)) continue;
+        if (!won<HASH>(a, nb, id)) continue;                   // lost, or never claimed
+        const BitPos bt = bitpos(a.geo, nb.i, nb.j, nb.k);
+        // the bit of a claimed voxel only changes through its winner, so it
+        // still tells a vacant target (hop) from a partner (reaction)
+        if (!GENERAL || !occupied(a.bits, bt)) {
+            bit_move(a.bits, bv, bt);                           // move (Sec. 2.3)
             if (a.live) {
-                a.occ[t] = self;
+                a.occ[nb.t] = self;
                 a.occ[v] = 0;
             }
-            a.list.vox[idx] = t;
-            if (w) a.list.img[idx] = img_add(a.list.img[idx], w);
+            a.list.vox[idx] = nb.t;
+            if (nb.wrap) a.list.img[idx] = img_add(a.list.img[idx], nb.wrap);
             ++n_hop;
         } else {
             // accepted collision with partner o - 1 (Sec. 2.4.2): first
             // product on the partner's voxel, second on the mover's
+            const uint16_t o = a.occ[nb.t];
             const ReactionDev R = a.model->rx[a.model->pair[a.s][o - 1]];
             if (R.np >= 1) {
-                a.occ[t] = (uint16_t)(R.p0 + 1);
+                a.occ[nb.t] = (uint16_t)(R.p0 + 1);
             } else {
-                a.occ[t] = 0;
-                bit_clear(a.bits, (uint32_t)t);
+                a.occ[nb.t] = 0;
+                bit_clear(a.bits, bt);
             }
             if (R.np == 2) {
                 a.occ[v] = (uint16_t)(R.p1 + 1);
             } else {
                 a.occ[v] = 0;
-                bit_clear(a.bits, v);
+                bit_clear(a.bits, bv);
             }
             ++n_r2;
         }
@@ -460,6 +549,290 @@ void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cu
 }
 
 // ---------------------------------------------------------------------------
+// persistent stretch of events of one species without reactions
+//
+// One cooperative launch sized to the SMs (see kRunShapes).  Thread x owns the
+// molecules x, x + T, x + 2T, ... (T threads in all) of the list for the whole
+// stretch and keeps their voxel, id and claim state in registers; each event
+// is claim phase -> grid barrier -> commit phase -> grid barrier.  A claimant
+// remembers the slot that holds its voxel's claim, so the commit phase reads
+// that one slot, and the next event's claim phase empties it again (the
+// tables alternate, so the table being emptied is not in use).
+// ---------------------------------------------------------------------------
+constexpr uint64_t kBarrierTimeoutNs = 1000000000ull;   // 1 s
+constexpr int kGroup = 1;                                  // molecules in flight per thread
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier: block 0 adds 2^31 - (blocks - 1), every other block adds 1,
+// so the top bit of the arrival word flips exactly when all have arrived.
+// The wait is bounded (about one second of wall time): on time-out the block
+// raises kErrBarrierTimeout and every thread of it returns false.
+__device__ __forceinline__ bool grid_barrier(BarrierState* bs, int32_t* err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        __threadfence();
+        const unsigned int old = atomicAdd(&bs->arrive, inc);
+        volatile unsigned int* word = &bs->arrive;
+        int good = 1;
+        uint64_t t0 = 0;
+        for (unsigned int spins = 0; ((old ^ *word) & 0x80000000u) == 0u; ++spins) {
+            if ((spins & 1023u) == 0u) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kBarrierTimeoutNs) {
+                    atomicOr(err, kErrBarrierTimeout);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// packed claim state of one molecule: bit 31 claimed, bits 27-30 direction,
+// bits 0-26 slot (hash tables of at most 2^27 slots).  A thread that leaves
+// through a failed barrier leaves the others to fail theirs within the same
+// bound; the host sees kErrBarrierTimeout.
+constexpr uint32_t kClaimed = 0x80000000u;
+
+template <bool HASH, int M, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_hop_run(const RunArgs r)
+{
+    // per-molecule state lives in shared memory, [m][thread] (conflict-free)
+    extern __shared__ uint32_t sm_state[];
+    uint32_t* s_vox = sm_state;
+    uint32_t* s_ids = sm_state + M * THREADS;
+    uint32_t* s_st = sm_state + 2 * M * THREADS;
+    const EventArgs& a = r.ev;
+    const int32_t n = *a.count;
+    const int T = gridDim.x * THREADS;
+    const int gt = blockIdx.x * THREADS + threadIdx.x;
+    const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
+    const uint16_t self = (uint16_t)(a.s + 1);
+    int mine = 0;                                   // molecules of this thread
+    for (int m = 0; m < M; ++m) {
+        const int idx = gt + m * T;
+        if (idx < n) {
+            s_vox[m * THREADS + threadIdx.x] = (uint32_t)a.list.vox[idx];
+            s_ids[m * THREADS + threadIdx.x] = a.list.ids[idx];
+            mine = m + 1;
+        }
+        s_st[m * THREADS + threadIdx.x] = 0u;
+    }
+    unsigned long long n_hop = 0;
+    for (int e = 0; e < r.n_events; ++e) {
+        const uint32_t g = a.g + (uint32_t)e;
+        uint64_t* tab = r.tables[g & 1u];
+        uint64_t* old = r.tables[(g & 1u) ^ 1u];
+        // ---- claim phase: kGroup molecules at a time, their loads and first
+        // claim attempts in flight together ----
+        for (int m0 = 0; m0 < mine; m0 += kGroup) {
+            Nb nb[kGroup];
+            BitPos bp[kGroup];
+            uint32_t idg[kGroup], stg[kGroup], home[kGroup], word[kGroup];
+            uint64_t hv[kGroup], prev[kGroup];
+            bool ok[kGroup], tried[kGroup];
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                const int m = m0 + x;
+                ok[x] = false;
+                tried[x] = false;
+                stg[x] = 0u;
+                idg[x] = 0u;
+                home[x] = 0u;
+                if (m >= mine) continue;
+                const int q = m * THREADS + threadIdx.x;
+                const uint32_t before = s_st[q];
+                if (HASH && (before & kClaimed)) old[before & 0x07FFFFFFu] = kEmptySlot;   // previous event
+                idg[x] = s_ids[q];
+                int32_t i, j, k;
+                decode(a.geo, s_vox[q], i, j, k);
+                uint32_t u[4];
+                philox(idg[x], g, c2, 0u, a.key0, a.key1, u);
+                const int d = (int)__umulhi(u[0], 12u);
+                stg[x] = (uint32_t)d << 27;
+                ok[x] = neighbor(a.geo, i, j, k, d, nb[x]);
+                if (ok[x]) {
+                    bp[x] = bitpos(a.geo, nb[x].i, nb[x].j, nb[x].k);
+                    if (HASH) home[x] = slot_of(a.geo, (uint32_t)nb[x].t, nb[x].i, nb[x].j, nb[x].k, a.ct.hash_bits);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                if (!ok[x]) continue;
+                word[x] = __ldcg(&a.bits[bp[x].word]);
+                if (HASH) hv[x] = __ldcg((const unsigned long long*)&tab[home[x]]);
+            }
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                ok[x] = ok[x] && !(word[x] & bp[x].mask);            // vacant target
+                if (!ok[x]) continue;
+                if (HASH) {
+                    if (hv[x] == kEmptySlot) {
+                        prev[x] = atomicCAS((unsigned long long*)&tab[home[x]], (unsigned long long)kEmptySlot,
+                                            (unsigned long long)(((uint64_t)nb[x].t << 32) | idg[x]));
+                        tried[x] = true;
+                    }
+                } else {
+                    atomicMin(&a.ct.direct[nb[x].t], idg[x]);
+                    stg[x] |= kClaimed;
+                }
+            }
+            if (HASH) {
+#pragma unroll
+                for (int x = 0; x < kGroup; ++x) {
+                    if (!ok[x]) continue;
+                    int32_t slot;
+                    if (tried[x] && prev[x] == kEmptySlot) slot = (int32_t)home[x];
+                    else slot = hash_claim_from(tab, a.ct.hash_bits, (uint32_t)nb[x].t, idg[x], home[x],
+                                                tried[x] ? prev[x] : hv[x], &a.sc->err);
+                    if (slot >= 0) stg[x] |= kClaimed | (uint32_t)slot;
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x)
+                if (m0 + x < mine) s_st[(m0 + x) * THREADS + threadIdx.x] = stg[x];
+        }
+        if (!grid_barrier(r.barrier, &a.sc->err)) return;
+        // ---- commit phase: slot reads of a group in flight together ----
+        for (int m0 = 0; m0 < mine; m0 += kGroup) {
+            uint32_t stg[kGroup], cw[kGroup];
+            uint64_t tv[kGroup];
+            Nb nb[kGroup];
+            int32_t ci[kGroup], cj[kGroup], ck[kGroup];
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                stg[x] = (m0 + x < mine) ? s_st[(m0 + x) * THREADS + threadIdx.x] : 0u;
+                if (HASH && (stg[x] & kClaimed)) tv[x] = __ldcg((const unsigned long long*)&tab[stg[x] & 0x07FFFFFFu]);
+            }
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                if (!(stg[x] & kClaimed)) continue;
+                decode(a.geo, s_vox[(m0 + x) * THREADS + threadIdx.x], ci[x], cj[x], ck[x]);
+                neighbor(a.geo, ci[x], cj[x], ck[x], (int)((stg[x] >> 27) & 15u), nb[x]);
+                if (!HASH) cw[x] = __ldcg(&a.ct.direct[nb[x].t]);
+            }
+#pragma unroll
+            for (int x = 0; x < kGroup; ++x) {
+                if (!(stg[x] & kClaimed)) continue;
+                const int q = (m0 + x) * THREADS + threadIdx.x;
+                const uint32_t id = s_ids[q];
+                bool win;
+                if (HASH) {
+                    win = (uint32_t)tv[x] == id;
+                } else {
+                    win = cw[x] == id;
+                    if (win) a.ct.direct[nb[x].t] = kNoClaim;
+                }
+                if (!win) continue;
+                const uint32_t v = s_vox[q];
+                bit_move(a.bits, bitpos(a.geo, ci[x], cj[x], ck[x]), bitpos(a.geo, nb[x].i, nb[x].j, nb[x].k));
+                if (a.live) {
+                    a.occ[nb[x].t] = self;
+                    a.occ[v] = 0;
+                }
+                if (nb[x].wrap) {
+                    const int idx = gt + (m0 + x) * T;
+                    a.list.img[idx] = img_add(a.list.img[idx], nb[x].wrap);
+                }
+                s_vox[q] = (uint32_t)nb[x].t;
+                ++n_hop;
+            }
+        }
+        if (!grid_barrier(r.barrier, &a.sc->err)) return;
+    }
+    // leave both tables empty: the last event's slots (the one before was
+    // emptied during the last claim phase)
+    if (HASH && r.n_events > 0) {
+        uint64_t* last = r.tables[(a.g + (uint32_t)r.n_events - 1u) & 1u];
+        for (int m = 0; m < mine; ++m) {
+            const uint32_t stq = s_st[m * THREADS + threadIdx.x];
+            if (stq & kClaimed) last[stq & 0x07FFFFFFu] = kEmptySlot;
+        }
+    }
+    for (int m = 0; m < mine; ++m) a.list.vox[gt + m * T] = (int32_t)s_vox[m * THREADS + threadIdx.x];
+    if (a.collect_stats) {
+        flush_stat(&a.sc->stats[kStatHops], n_hop);
+        flush_stat(&a.sc->stats[kStatAttempts], (unsigned long long)mine * (unsigned long long)r.n_events);
+    }
+}
+
+// Launch shapes: two 768-thread blocks per SM (<= 42 registers) with up to 6
+// molecules per thread, or one 768-thread block per SM with up to 24
+// (3 x 24 x 768 words = 216 KB of shared memory).  More resident threads
+// beat more molecules in flight per thread here (measured: the kernel is
+// bound by L2 operations, not by per-thread latency chains).
+struct RunShape {
+    int per_thread, threads, blocks_per_sm;
+};
+static const RunShape kRunShapes[] = {
+    {2, 768, 2}, {4, 768, 2}, {6, 768, 2}, {8, 768, 1}, {12, 768, 1}, {16, 768, 1}, {24, 768, 1}};
+
+int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count)
+{
+    for (const RunShape& sh : kRunShapes) {
+        const int64_t T = (int64_t)sh.threads * sh.blocks_per_sm * sm_count;
+        if (n <= (int64_t)sh.per_thread * T) {
+            *threads_per_block = sh.threads;
+            *blocks = sh.blocks_per_sm * sm_count;
+            return sh.per_thread;
+        }
+    }
+    return 0;
+}
+
+template <bool HASH, int M, int THREADS, int MINB>
+static cudaError_t launch_run_t(const RunArgs& r, int blocks, int threads, cudaStream_t st)
+{
+    if (threads != THREADS) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)3 * M * THREADS * sizeof(uint32_t);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_hop_run<HASH, M, THREADS, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    void* args[] = {const_cast<RunArgs*>(&r)};
+    return cudaLaunchCooperativeKernel((const void*)k_hop_run<HASH, M, THREADS, MINB>, dim3(blocks), dim3(threads),
+                                       args, smem, st);
+}
+
+template <bool HASH>
+static cudaError_t launch_run_h(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st)
+{
+    switch (per_thread) {
+    case 2: return launch_run_t<HASH, 2, 768, 2>(r, blocks, threads, st);
+    case 4: return launch_run_t<HASH, 4, 768, 2>(r, blocks, threads, st);
+    case 6: return launch_run_t<HASH, 6, 768, 2>(r, blocks, threads, st);
+    case 8: return launch_run_t<HASH, 8, 768, 1>(r, blocks, threads, st);
+    case 12: return launch_run_t<HASH, 12, 768, 1>(r, blocks, threads, st);
+    case 16: return launch_run_t<HASH, 16, 768, 1>(r, blocks, threads, st);
+    case 24: return launch_run_t<HASH, 24, 768, 1>(r, blocks, threads, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st)
+{
+    return r.ev.ct.hash ? launch_run_h<true>(r, blocks, threads, per_thread, st)
+                        : launch_run_h<false>(r, blocks, threads, per_thread, st);
+}
+
+// ---------------------------------------------------------------------------
 // reconcile: bring the list of species x in line with the grid after an event
 // with reactions.  An entry whose voxel holds x stays; one whose voxel holds
 // species y (a product that inherited this molecule's identity) moves to y's
@@ -492,7 +865,9 @@ __global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
             v = r.list.vox[idx];
             id = r.list.ids[idx];
             img = r.list.img[idx];
-            o = ((r.bits[(uint32_t)v >> 5] >> ((uint32_t)v & 31u)) & 1u) ? r.occ[v] : (uint16_t)0;
+            int32_t i, j, k;
+            decode(r.geo, (uint32_t)v, i, j, k);
+            o = occupied(r.bits, bitpos(r.geo, i, j, k)) ? r.occ[v] : (uint16_t)0;
         }
         const bool keep = valid && o == self;
         const int slot = warp_alloc(&r.sc->tmp_count[r.x], keep);
@@ -630,16 +1005,19 @@ void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStre
 // exact species grid for read-out: the codes of species with reactions where
 // the mirror says occupied, zero elsewhere; species without reactions are
 // written afterwards from their lists (they do not keep codes while moving)
-__global__ void k_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V)
+__global__ void k_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, Geometry G, int64_t V)
 {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
-        out[v] = ((bits[v >> 5] >> (v & 31)) & 1u) ? occ[v] : (uint16_t)0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i, j, k;
+        decode(G, (uint32_t)v, i, j, k);
+        out[v] = occupied(bits, bitpos(G, i, j, k)) ? occ[v] : (uint16_t)0;
+    }
 }
 
-void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, int64_t V, int blocks,
-                        cudaStream_t st)
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
+                        int64_t V, int blocks, cudaStream_t st)
 {
-    k_materialize<<<blocks, 256, 0, st>>>(out, occ, bits, V);
+    k_materialize<<<blocks, 256, 0, st>>>(out, occ, bits, geo, V);
 }
 
 __global__ void k_scatter_codes(uint16_t* out, const SpeciesList L, const int32_t* count, uint16_t code)
@@ -678,7 +1056,7 @@ struct Offsets {
 
 // rank r of the sorted voxels goes to the species whose range holds r
 __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, Offsets o, int n_species,
-                                   uint16_t* occ, uint32_t* bits, const ModelDev* model)
+                                   uint16_t* occ, uint32_t* bits, Geometry G, const ModelDev* model)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_total;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -687,7 +1065,9 @@ __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, 
         const uint32_t v = sorted_vox[r];
         const int64_t a = r - o.off[s];
         occ[v] = (uint16_t)(s + 1);
-        atomicOr(&bits[v >> 5], 1u << (v & 31u));
+        int32_t i, j, k;
+        decode(G, v, i, j, k);
+        bit_set(bits, bitpos(G, i, j, k));
         const SpeciesList L = model->lists[s];
         L.vox[a] = (int32_t)v;
         L.ids[a] = (uint32_t)r;
@@ -696,34 +1076,22 @@ __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, 
 }
 
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, uint32_t* bits, const ModelDev* model,
-                             int blocks, cudaStream_t st)
+                             int n_species, uint16_t* occ, uint32_t* bits, const Geometry& geo,
+                             const ModelDev* model, int blocks, cudaStream_t st)
 {
     Offsets o;
     for (int s = 0; s <= kMaxSpecies; ++s) o.off[s] = s <= n_species ? offsets[s] : offsets[n_species];
-    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, n_species, occ, bits, model);
+    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, n_species, occ, bits, geo, model);
 }
 
-// Morton (Z-order) key of the voxel of each list entry, 10 bits per axis
-__device__ __forceinline__ uint32_t spread3(uint32_t x)
-{
-    x &= 0x3FFu;
-    x = (x | (x << 16)) & 0x030000FFu;
-    x = (x | (x << 8)) & 0x0300F00Fu;
-    x = (x | (x << 4)) & 0x030C30C3u;
-    x = (x | (x << 2)) & 0x09249249u;
-    return x;
-}
-
-__global__ void k_morton_keys(const SpeciesList L, const int32_t* count, Geometry G, int shift,
-                              uint32_t* keys, uint32_t* vals)
+// Morton (Z-order) key of the voxel of each list entry (compact code)
+__global__ void k_morton_keys(const SpeciesList L, const int32_t* count, Geometry G, uint32_t* keys, uint32_t* vals)
 {
     const int32_t n = *count;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int32_t i, j, k;
         decode(G, (uint32_t)L.vox[idx], i, j, k);
-        keys[idx] = spread3((uint32_t)i >> shift) | (spread3((uint32_t)j >> shift) << 1) |
-                    (spread3((uint32_t)k >> shift) << 2);
+        keys[idx] = morton(G, i, j, k);
         vals[idx] = (uint32_t)idx;
     }
 }
@@ -731,12 +1099,10 @@ __global__ void k_morton_keys(const SpeciesList L, const int32_t* count, Geometr
 void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st)
 {
-    int maxdim = geo.ni > geo.nj ? geo.ni : geo.nj;
-    if (geo.nk > maxdim) maxdim = geo.nk;
-    int shift = 0;
-    while ((maxdim - 1) >> shift >= 1024) ++shift;
-    k_morton_keys<<<blocks, 256, 0, st>>>(list, count, geo, shift, keys, vals);
+    k_morton_keys<<<blocks, 256, 0, st>>>(list, count, geo, keys, vals);
 }
+
+uint32_t morton_sort_bits(const Geometry& geo) { return geo.mort_bits; }
 
 __global__ void k_permute(const SpeciesList src, const SpeciesList dst, const uint32_t* perm, const int32_t* count)
 {

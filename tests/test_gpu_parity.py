@@ -65,12 +65,13 @@ def test_ab_to_c_64cubed_full_run(seed):
         assert_same(g, o, "t=%d tau" % t)
 
 
+@pytest.mark.parametrize("persistent", [1, -1])
 @pytest.mark.parametrize("claim_table", [1, 2])
 @pytest.mark.parametrize("shape,frac", [((96, 80, 64), 0.01), ((37, 24, 18), 0.30), ((50, 44, 30), 0.60)])
-def test_diffusion_ragged_shapes(shape, frac, claim_table):
+def test_diffusion_ragged_shapes(shape, frac, claim_table, persistent):
     V = shape[0] * shape[1] * shape[2]
     g, o = build_both(shape, lambda L: models.diffusion_only(L, int(frac * V)), 11, resort_period=7,
-                      claim_table=claim_table)
+                      claim_table=claim_table, persistent=persistent)
     for _ in range(4):
         g.run_events(13)
         o.run_events(13)
@@ -203,8 +204,9 @@ def test_results_do_not_depend_on_launch_shape_or_resort():
             assert np.array_equal(a, c) and np.array_equal(b, d)
 
 
-def test_diffusion_256cubed_one_percent():
-    g, o = build_both((256, 256, 256), lambda L: models.diffusion_only(L, 167772), 2)
+@pytest.mark.parametrize("persistent", [1, -1])
+def test_diffusion_256cubed_one_percent(persistent):
+    g, o = build_both((256, 256, 256), lambda L: models.diffusion_only(L, 167772), 2, persistent=persistent)
     for _ in range(2):
         g.run_events(10)
         o.run_events(10)

@@ -246,6 +246,45 @@ typedef void *(*psc_alloc_fn)(size_t bytes, int device, void *stream, void *ctx)
 typedef void (*psc_free_fn)(void *ptr, int device, void *stream, void *ctx);
 int psc_set_allocator(psc_alloc_fn alloc, psc_free_fn release, void *ctx);
 
+/*
+ * psc_hop_events_static -- n_events diffusion events of one species that has
+ * no reactions, on molecule buffers the caller owns, without allocating any
+ * memory.  (The paper has no counterpart: this is a deployment variant of
+ * the claim/commit kernels of psc_run_events.)
+ *
+ * For callers that cannot allocate device memory when they step molecules --
+ * a framework that owns all device memory through its own pool, code running
+ * under an allocator lock, or code that must not trigger the synchronisation
+ * cudaMalloc/cudaFree may cause.  The claim words, the vacancy mirror and the
+ * counters live in fixed-size device arrays inside the library, which every
+ * GPU that loads the library holds until the process exits (about 12 MiB).
+ *
+ *   ni, nj, nk, boundary_flags   lattice as for psc_lattice_create; at most
+ *                    2^21 voxels (e.g. 128^3) and a vacancy mirror of at most
+ *                    2^20 words, else PSC_E_CAPACITY.
+ *   seed, species    Philox key and species index of the draws; with
+ *                    first_event the event index of the first event, so the
+ *                    results equal psc_run_events on a lattice holding the
+ *                    same molecules with the same seed (bit for bit).
+ *   vox              device, n entries, in/out: voxel index of each molecule.
+ *   ids              device, n entries, in: molecule ids.
+ *   img              device, n entries, in/out: packed 16-bit wrap counters
+ *                    (i bits 0-15, j 16-31, k 32-47); zeros if unused.
+ *   n                molecules (the only occupied voxels of the lattice).
+ *   stream           cudaStream_t (NULL = default stream).
+ * Work is queued on the stream; the call returns once it is queued.  The first
+ * call on each device looks up the addresses of the internal arrays
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  Every call clears the internal arrays it uses, but all calls on a
+ * device share them: calls that may overlap on the GPU (different streams, or
+ * host threads) race and must be serialised by the caller.
+ * Errors: PSC_E_ARG, PSC_E_DIMS, PSC_E_FULL, PSC_E_LIMIT, PSC_E_CAPACITY,
+ * PSC_E_CUDA.
+ */
+int psc_hop_events_static(int32_t ni, int32_t nj, int32_t nk, uint32_t boundary_flags,
+                          uint64_t seed, int32_t species, uint32_t first_event, int32_t n_events,
+                          int32_t *vox, const uint32_t *ids, uint64_t *img, int32_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ def lib():
             "psc_lattice_destroy": (None, [P]),
             "psc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "psc_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, P]),
+            "psc_hop_events_static": (ctypes.c_int, [i32, i32, i32, u32, u64, i32, u32, i32, P, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -100,7 +101,8 @@ EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_po
             "psc_run_events", "psc_synchronize", "psc_counts", "psc_coords", "psc_unwrapped", "psc_grid",
             "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_kernel_times_get",
             "psc_tau", "psc_p_ab",
-            "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator")
+            "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator",
+            "psc_hop_events_static")
 
 
 class EngineError(RuntimeError):

@@ -193,6 +193,9 @@ void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32
                     const int32_t* count, int blocks, cudaStream_t st);
 void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count,
                       int blocks, cudaStream_t st);
+// set the vacancy-mirror bit of every molecule of a list (mirror cleared before)
+void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesList& list, const int32_t* count,
+                             int blocks, cudaStream_t st);
 
 // ---- radix sort (psc_sort.cu) ----
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.

@@ -1137,4 +1137,20 @@ void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int3
     k_copy_list<<<blocks, 256, 0, st>>>(src, dst, count);
 }
 
+__global__ void k_mirror_from_list(uint32_t* bits, Geometry G, const SpeciesList L, const int32_t* count)
+{
+    const int32_t n = *count;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        int32_t i, j, k;
+        decode(G, (uint32_t)L.vox[x], i, j, k);
+        bit_set(bits, bitpos(G, i, j, k));
+    }
+}
+
+void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesList& list, const int32_t* count,
+                             int blocks, cudaStream_t st)
+{
+    k_mirror_from_list<<<blocks, 256, 0, st>>>(bits, geo, list, count);
+}
+
 }  // namespace psc

@@ -247,6 +247,78 @@ typedef void (*psc_free_fn)(void *ptr, int device, void *stream, void *ctx);
 int psc_set_allocator(psc_alloc_fn alloc, psc_free_fn release, void *ctx);
 
 /*
+ * Batches: many lattices (replicas, parameter sweeps) advanced together.
+ * Every launch of a batch covers all its members, each running its own next
+ * event (its own species and event index), so a batch of small lattices costs
+ * about as many launches per event as one lattice.  Results of a member are
+ * bit-identical to running it alone (same seed, same model).
+ *
+ *   psc_batch_create   cuda_stream as for psc_lattice_create.
+ *   psc_batch_add      L must be populated, on the batch's device and stream
+ *                      (create it with the same cuda_stream), and use one
+ *                      claim word per voxel (lattices up to 2^22 voxels by
+ *                      default, or psc_options.claim_table = 1); at most 512
+ *                      members.  The batch does not own L.
+ *   psc_batch_run_events   every member runs n_events more of its events.
+ *   psc_batch_run      every member runs its events with time <= t_end.
+ * Errors: PSC_E_ARG, PSC_E_ORDER (not populated), PSC_E_UNSUPPORTED (hash
+ * claim table, other device or stream), PSC_E_CAPACITY (batch full), PSC_E_CUDA.
+ */
+typedef struct psc_batch psc_batch;
+int  psc_batch_create(psc_batch **out, int device, void *cuda_stream);
+int  psc_batch_add(psc_batch *B, psc_lattice *L);
+int  psc_batch_remove(psc_batch *B, psc_lattice *L);
+int  psc_batch_size(const psc_batch *B, int32_t *n);
+int  psc_batch_run_events(psc_batch *B, int64_t n_events);
+int  psc_batch_run(psc_batch *B, double t_end);
+int64_t psc_batch_launches(const psc_batch *B);
+void psc_batch_destroy(psc_batch *B);
+
+/*
+ * Serving: a request loop with continuous batching.  A request describes a
+ * whole simulation (lattice, species, reactions, seed, end time); submitted
+ * requests wait in FIFO order and are admitted while the device memory they
+ * need (psc_device_bytes) fits under max_device_bytes and fewer than
+ * max_active run.  psc_server_step admits what fits, advances every admitted
+ * simulation by up to n_events of its events in batched launches, and
+ * retires the ones that reached their end time (their counts are kept, their
+ * memory freed), so requests that arrive while others run join the batch as
+ * slots and memory free up.  A result is the same alone and in any mix.
+ *   psc_request arrays: D and initial_count have n_species entries; per
+ *   reaction r: n_reactants[r] (1|2) reactants at reactants[2r..], n_products[r]
+ *   (0..2) products at products[2r..], rate k[r].
+ *   psc_server_result: counts at the end time and the seconds from submit to
+ *   retirement; PSC_E_ORDER while the request is not finished; the stored
+ *   error of a request that failed.
+ */
+typedef struct {
+    int32_t ni, nj, nk;
+    uint32_t boundary_flags;
+    double voxel_radius_m;
+    int32_t n_species;
+    const double *D;
+    const int64_t *initial_count;
+    int32_t n_reactions;
+    const int32_t *n_reactants;
+    const int32_t *reactants;
+    const int32_t *n_products;
+    const int32_t *products;
+    const double *k;
+    uint64_t seed;
+    double t_end;
+} psc_request;
+
+typedef struct psc_server psc_server;
+int  psc_server_create(psc_server **out, int device, void *cuda_stream, int64_t max_device_bytes,
+                       int32_t max_active);
+int  psc_server_submit(psc_server *S, const psc_request *req, int64_t *ticket);
+int  psc_server_step(psc_server *S, int32_t n_events, int32_t *n_active, int32_t *n_waiting);
+int  psc_server_result(psc_server *S, int64_t ticket, int64_t *counts, int32_t n_species,
+                       double *seconds_to_result);
+int  psc_server_memory(const psc_server *S, int64_t *bytes_in_use, int64_t *peak_bytes);
+void psc_server_destroy(psc_server *S);
+
+/*
  * psc_hop_events_static -- n_events diffusion events of one species that has
  * no reactions, on molecule buffers the caller owns, without allocating any
  * memory.  (The paper has no counterpart: this is a deployment variant of

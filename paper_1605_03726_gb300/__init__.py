@@ -49,6 +49,15 @@ class KernelTimes(ctypes.Structure):
                 for n, t in self._fields_}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int32), ("nj", ctypes.c_int32), ("nk", ctypes.c_int32),
+                ("boundary_flags", ctypes.c_uint32), ("voxel_radius_m", ctypes.c_double),
+                ("n_species", ctypes.c_int32), ("D", ctypes.c_void_p), ("initial_count", ctypes.c_void_p),
+                ("n_reactions", ctypes.c_int32), ("n_reactants", ctypes.c_void_p), ("reactants", ctypes.c_void_p),
+                ("n_products", ctypes.c_void_p), ("products", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("t_end", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -88,6 +97,20 @@ def lib():
             "psc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "psc_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, P]),
             "psc_hop_events_static": (ctypes.c_int, [i32, i32, i32, u32, u64, i32, u32, i32, P, P, P, i32, P]),
+            "psc_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+            "psc_batch_add": (ctypes.c_int, [P, P]),
+            "psc_batch_remove": (ctypes.c_int, [P, P]),
+            "psc_batch_size": (ctypes.c_int, [P, ctypes.POINTER(i32)]),
+            "psc_batch_run_events": (ctypes.c_int, [P, i64]),
+            "psc_batch_run": (ctypes.c_int, [P, dbl]),
+            "psc_batch_launches": (i64, [P]),
+            "psc_batch_destroy": (None, [P]),
+            "psc_server_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P, i64, i32]),
+            "psc_server_submit": (ctypes.c_int, [P, ctypes.POINTER(Request), ctypes.POINTER(i64)]),
+            "psc_server_step": (ctypes.c_int, [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "psc_server_result": (ctypes.c_int, [P, i64, P, i32, ctypes.POINTER(dbl)]),
+            "psc_server_memory": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "psc_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -102,7 +125,10 @@ EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_po
             "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_kernel_times_get",
             "psc_tau", "psc_p_ab",
             "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator",
-            "psc_hop_events_static")
+            "psc_hop_events_static", "psc_batch_create", "psc_batch_add", "psc_batch_remove", "psc_batch_size",
+            "psc_batch_run_events", "psc_batch_run", "psc_batch_launches", "psc_batch_destroy",
+            "psc_server_create", "psc_server_submit", "psc_server_step", "psc_server_result", "psc_server_memory",
+            "psc_server_destroy")
 
 
 class EngineError(RuntimeError):
@@ -265,3 +291,104 @@ class Lattice:
         b = ctypes.c_int64()
         _check("psc_device_bytes", lib().psc_device_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+
+class Batch:
+    """Lattices advanced together by shared launches (psc_batch_*)."""
+
+    def __init__(self, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        _check("psc_batch_create", lib().psc_batch_create(ctypes.byref(self._h), device,
+                                                          ctypes.c_void_p(stream) if stream else None))
+        self.members = []
+
+    def add(self, lattice):
+        _check("psc_batch_add", lib().psc_batch_add(self._h, lattice._h))
+        self.members.append(lattice)
+
+    def remove(self, lattice):
+        _check("psc_batch_remove", lib().psc_batch_remove(self._h, lattice._h))
+        self.members.remove(lattice)
+
+    def run_events(self, n):
+        _check("psc_batch_run_events", lib().psc_batch_run_events(self._h, int(n)))
+
+    def run(self, t_end):
+        _check("psc_batch_run", lib().psc_batch_run(self._h, float(t_end)))
+
+    def launches(self):
+        return int(lib().psc_batch_launches(self._h))
+
+    def close(self):
+        if self._h:
+            lib().psc_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop with continuous batching (psc_server_*)."""
+
+    def __init__(self, max_device_bytes, max_active=512, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        _check("psc_server_create", lib().psc_server_create(
+            ctypes.byref(self._h), device, ctypes.c_void_p(stream) if stream else None, int(max_device_bytes),
+            int(max_active)))
+        self._keep = {}
+
+    def submit(self, shape, D, counts, reactions, seed, t_end, voxel_radius=10e-9, boundary=PERIODIC_ALL):
+        """reactions: list of (reactants, products, k)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        n0 = np.ascontiguousarray(counts, dtype=np.int64)
+        nr = len(reactions)
+        nre = np.array([len(r[0]) for r in reactions] or [0], dtype=np.int32)
+        npr = np.array([len(r[1]) for r in reactions] or [0], dtype=np.int32)
+        re = np.zeros(2 * max(1, nr), dtype=np.int32)
+        pr = np.zeros(2 * max(1, nr), dtype=np.int32)
+        kk = np.array([r[2] for r in reactions] or [0.0], dtype=np.float64)
+        for x, (a, b, _) in enumerate(reactions):
+            re[2 * x: 2 * x + len(a)] = a
+            pr[2 * x: 2 * x + len(b)] = b
+        req = Request(shape[0], shape[1], shape[2], boundary, voxel_radius, len(D), _ptr(D), _ptr(n0), nr,
+                      _ptr(nre), _ptr(re), _ptr(npr), _ptr(pr), _ptr(kk), int(seed), float(t_end))
+        t = ctypes.c_int64()
+        _check("psc_server_submit", lib().psc_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = len(D)
+        return t.value
+
+    def step(self, n_events):
+        a, w = ctypes.c_int32(), ctypes.c_int32()
+        _check("psc_server_step", lib().psc_server_step(self._h, int(n_events), ctypes.byref(a), ctypes.byref(w)))
+        return a.value, w.value
+
+    def result(self, ticket):
+        """(counts, seconds_to_result), or None while the request runs."""
+        n = self._keep[ticket]
+        c = np.zeros(n, dtype=np.int64)
+        sec = ctypes.c_double()
+        rc = lib().psc_server_result(self._h, ticket, _ptr(c), n, ctypes.byref(sec))
+        if rc == E_ORDER:
+            return None
+        _check("psc_server_result", rc)
+        return c, sec.value
+
+    def memory(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check("psc_server_memory", lib().psc_server_memory(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if self._h:
+            lib().psc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

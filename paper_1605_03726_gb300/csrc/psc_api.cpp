@@ -8,6 +8,7 @@
 // from device memory, so the host never waits for the device between events.
 #include "psc.h"
 #include "psc_internal.h"
+#include "psc_runtime.h"
 
 #include <algorithm>
 #include <cmath>
@@ -25,22 +26,6 @@ psc_alloc_fn g_alloc = nullptr;
 psc_free_fn g_free = nullptr;
 void* g_alloc_ctx = nullptr;
 std::mutex g_alloc_mu;
-
-struct Species {
-    double D = 0.0;
-    int64_t n0 = 0;
-    double tau = 0.0;
-    uint64_t done = 0;
-    int n_fo = 0;
-    int fo[kMaxFirstOrder] = {};
-};
-
-struct Reaction {
-    int nr = 0, np = 0;
-    int r[2] = {0, 0}, p[2] = {0, 0};
-    double k = 0.0;
-    double prob = 0.0;
-};
 
 // floor(min(p, 1) * 2^32): a 32-bit uniform u passes with probability p iff u < T
 uint64_t prob_threshold(double p)
@@ -61,69 +46,7 @@ double acceptance(double k, double DA, double DB, double rv)
 
 }  // namespace
 
-struct psc_lattice {
-    int32_t ni = 0, nj = 0, nk = 0;
-    int64_t V = 0;
-    double rv = 0.0;
-    uint32_t bflags = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int sm_count = 0;
-
-    int nsp = 0;
-    Species sp[kMaxSpecies];
-    int nrx = 0;
-    Reaction rx[kMaxReactions];
-    int8_t pair[kMaxSpecies][kMaxSpecies];
-
-    bool populated = false;
-    bool clamped = false;
-    uint64_t seed = 0;
-    uint32_t g = 0;
-    double clock = 0.0;
-
-    Geometry geo{};
-    ModelDev model_h{};
-    ModelDev* model_d = nullptr;
-    uint16_t* occ = nullptr;
-    uint32_t* bits = nullptr;          // vacancy mirror, one bit per voxel
-    uint32_t* claim = nullptr;         // per-voxel claim words (small lattices)
-    uint64_t* tables[2] = {nullptr, nullptr};   // claim hash tables (large lattices)
-    uint32_t table_used[2] = {0, 0};   // slots written by the event that used it
-    int64_t table_slots = 0;
-    BarrierState* barrier = nullptr;
-    uint32_t hash_bits[kMaxSpecies] = {};
-    Scalars* sc = nullptr;
-    Birth* births = nullptr;
-    int32_t births_cap = 0;
-    SpeciesList tmp{};
-    int32_t cap[kMaxSpecies] = {};
-    uint32_t* rs_keys = nullptr;      // re-sort keys / values
-    uint32_t* rs_vals = nullptr;
-    SortScratch rs_scratch;
-    int64_t rs_max = 0;
-
-    bool general[kMaxSpecies] = {};
-    bool live[kMaxSpecies] = {};       // takes part in a reaction: keeps its codes
-    bool fo2[kMaxSpecies] = {};
-    std::vector<int> reconcile[kMaxSpecies];
-    uint64_t since_resort[kMaxSpecies] = {};
-
-    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3};
-    int64_t launches = 0;
-    uint64_t events = 0;
-    uint64_t h2d = 0, d2h = 0;
-
-    // CUDA-event spans around kernels (psc_options.time_kernels)
-    struct Span { cudaEvent_t a, b; int kind; int64_t events; };
-    std::vector<Span> spans;
-    std::vector<cudaEvent_t> event_pool;
-    int sticky = PSC_OK;
-    std::vector<void*> allocs;
-};
-
-namespace {
+namespace psc_rt {
 
 int cuda_fail(psc_lattice* L, cudaError_t e)
 {
@@ -251,6 +174,20 @@ int resort(psc_lattice* L, int s)
     return PSC_OK;
 }
 
+ReconcileArgs reconcile_args(const psc_lattice* L, int x)
+{
+    ReconcileArgs r{};
+    r.geo = L->geo;
+    r.occ = L->occ;
+    r.bits = L->bits;
+    r.x = x;
+    r.list = L->model_h.lists[x];
+    r.tmp = L->tmp;
+    r.model = L->model_d;
+    r.sc = L->sc;
+    return r;
+}
+
 int enqueue_event(psc_lattice* L, int s)
 {
     const EventArgs a = event_args(L, s);
@@ -270,15 +207,7 @@ int enqueue_event(psc_lattice* L, int s)
     }
     sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
     for (int x : L->reconcile[s]) {
-        ReconcileArgs r{};
-        r.geo = L->geo;
-        r.occ = L->occ;
-        r.bits = L->bits;
-        r.x = x;
-        r.list = L->model_h.lists[x];
-        r.tmp = L->tmp;
-        r.model = L->model_d;
-        r.sc = L->sc;
+        const ReconcileArgs r = reconcile_args(L, x);
         const int rb = event_blocks(L, L->cap[x]);
         launch_reconcile(r, rb, threads, L->stream);
         launch_copyback(r, rb, threads, L->stream);
@@ -365,13 +294,11 @@ int check_device(psc_lattice* L)
     return L->sticky;
 }
 
-struct DevGuard {
-    int prev = -1;
-    explicit DevGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
-    ~DevGuard() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
-};
 
-}  // namespace
+
+}  // namespace psc_rt
+
+using namespace psc_rt;
 
 extern "C" {
 

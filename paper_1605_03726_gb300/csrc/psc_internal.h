@@ -197,6 +197,28 @@ void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int3
 void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesList& list, const int32_t* count,
                              int blocks, cudaStream_t st);
 
+// ---- batched launches: many lattices (replicas) per launch ----
+// Item x covers blocks [block0, next block0) of the launch and runs the event
+// (or list) `sel` of replica `rep` with event index g.  Argument templates of
+// every (replica, species) live on the device: tmpl[rep * kMaxSpecies + sel].
+constexpr int kBatchMax = 512;
+struct BatchItem {
+    int32_t rep;
+    int32_t sel;
+    uint32_t g;
+    int32_t block0;
+};
+struct BatchLaunch {
+    int32_t n;
+    int32_t total_blocks;
+    BatchItem item[kBatchMax];
+};
+void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+
 // ---- radix sort (psc_sort.cu) ----
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
 // n is read from device memory (n_dev) or taken from n_host when n_dev is

@@ -341,15 +341,17 @@ __device__ __forceinline__ bool won(const EventArgs& a, const Nb& nb, uint32_t i
 // ---------------------------------------------------------------------------
 // claim
 // ---------------------------------------------------------------------------
+// The body of each event kernel takes its block index and block count
+// explicitly, so a batched launch can hand each replica a range of blocks.
 template <bool GENERAL, bool HASH>
-__global__ void __launch_bounds__(256) k_claim(const EventArgs a)
+__device__ __forceinline__ void claim_body(const EventArgs& a, uint32_t g, int blk, int nblk)
 {
     const int32_t n = *a.count;
-    if (blockIdx.x == 0 && threadIdx.x < kMaxSpecies) a.sc->tmp_count[threadIdx.x] = 0;
+    if (blk == 0 && threadIdx.x < kMaxSpecies) a.sc->tmp_count[threadIdx.x] = 0;
     unsigned long long n_att = 0, n_col = 0, n_acc = 0, n_fire = 0;
     const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int stride = nblk * blockDim.x;
+    for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
         const uint32_t v = (uint32_t)a.list.vox[idx];
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
         int32_t i, j, k;
         decode(a.geo, v, i, j, k);
         uint32_t u[4];
-        philox(id, a.g, c2, 0u, a.key0, a.key1, u);
+        philox(id, g, c2, 0u, a.key0, a.key1, u);
         ++n_att;
         if (GENERAL) {
             const ModelDev* M = a.model;
@@ -414,23 +416,29 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
     }
 }
 
+template <bool GENERAL, bool HASH>
+__global__ void __launch_bounds__(256) k_claim(const EventArgs a)
+{
+    claim_body<GENERAL, HASH>(a, a.g, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // commit
 // ---------------------------------------------------------------------------
 template <bool GENERAL, bool HASH>
-__global__ void __launch_bounds__(256) k_commit(const EventArgs a)
+__device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int blk, int nblk)
 {
     const int32_t n = *a.count;
     unsigned long long n_hop = 0, n_r2 = 0, n_r1 = 0;
     const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
     const uint16_t self = (uint16_t)(a.s + 1);
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = nblk * blockDim.x;
     if (HASH) {
         // empty the table of the previous event for the next one
-        for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < a.ct.clear_n; x += stride)
+        for (uint32_t x = blk * blockDim.x + threadIdx.x; x < a.ct.clear_n; x += stride)
             a.ct.clear[x] = kEmptySlot;
     }
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
         const uint32_t v = (uint32_t)a.list.vox[idx];
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
         decode(a.geo, v, i, j, k);
         const BitPos bv = bitpos(a.geo, i, j, k);
         uint32_t u[4];
-        philox(id, a.g, c2, 0u, a.key0, a.key1, u);
+        philox(id, g, c2, 0u, a.key0, a.key1, u);
         if (GENERAL) {
             const ModelDev* M = a.model;
             if (M->n_fo[a.s] > 0 && (uint64_t)u[2] < M->T_fire[a.s]) {
@@ -522,6 +530,12 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
             flush_stat(&a.sc->stats[kStatReactions1], n_r1);
         }
     }
+}
+
+template <bool GENERAL, bool HASH>
+__global__ void __launch_bounds__(256) k_commit(const EventArgs a)
+{
+    commit_body<GENERAL, HASH>(a, a.g, blockIdx.x, gridDim.x);
 }
 
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)
@@ -852,12 +866,12 @@ __device__ __forceinline__ int warp_alloc(int* counter, bool want)
     return want ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
-__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
+__device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, int blk, int nblk)
 {
     const int32_t n = r.sc->counts[r.x];
     const uint16_t self = (uint16_t)(r.x + 1);
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int stride = nblk * blockDim.x;
+    for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         const bool valid = idx < n;
         int32_t v = 0; uint32_t id = 0; uint64_t img = 0; uint16_t o = 0;
@@ -890,16 +904,26 @@ __global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
     }
 }
 
-__global__ void __launch_bounds__(256) k_copyback(const ReconcileArgs r)
+__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
+{
+    reconcile_body(r, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void copyback_body(const ReconcileArgs& r, int blk, int nblk)
 {
     const int32_t m = r.sc->tmp_count[r.x];
-    if (blockIdx.x == 0 && threadIdx.x == 0) r.sc->counts[r.x] = m;
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m; idx += stride) {
+    if (blk == 0 && threadIdx.x == 0) r.sc->counts[r.x] = m;
+    const int stride = nblk * blockDim.x;
+    for (int idx = blk * blockDim.x + threadIdx.x; idx < m; idx += stride) {
         r.list.vox[idx] = r.tmp.vox[idx];
         r.list.ids[idx] = r.tmp.ids[idx];
         r.list.img[idx] = r.tmp.img[idx];
     }
+}
+
+__global__ void __launch_bounds__(256) k_copyback(const ReconcileArgs r)
+{
+    copyback_body(r, blockIdx.x, gridDim.x);
 }
 
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
@@ -918,7 +942,7 @@ void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream
 // ---------------------------------------------------------------------------
 constexpr int kBirthSortMax = 8192;
 
-__global__ void __launch_bounds__(1024) k_births(const EventArgs a)
+__device__ __forceinline__ void births_body(const EventArgs& a)
 {
     extern __shared__ unsigned long long keys[];
     int nb = a.sc->births;
@@ -964,6 +988,11 @@ __global__ void __launch_bounds__(1024) k_births(const EventArgs a)
         if (a.collect_stats) a.sc->stats[kStatBirths] += (unsigned long long)nb;
         a.sc->births = 0;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_births(const EventArgs a)
+{
+    births_body(a);
 }
 
 void launch_births(const EventArgs& a, cudaStream_t st)
@@ -1151,6 +1180,94 @@ void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesL
                              int blocks, cudaStream_t st)
 {
     k_mirror_from_list<<<blocks, 256, 0, st>>>(bits, geo, list, count);
+}
+
+// ---------------------------------------------------------------------------
+// batched launches: every active replica runs its own next event (or list
+// pass) inside one launch; block b belongs to the item whose block range
+// holds it.  Replicas in a batch use per-voxel claim words.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_find(const BatchLaunch& bl, int b, int* nblk)
+{
+    int lo = 0, hi = bl.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bl.item[mid].block0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    *nblk = (lo + 1 < bl.n ? bl.item[lo + 1].block0 : bl.total_blocks) - bl.item[lo].block0;
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_claim_batch(const EventArgs* tmpl, const BatchLaunch bl)
+{
+    int nblk;
+    const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
+    const EventArgs a = tmpl[I.rep * kMaxSpecies + I.sel];
+    claim_body<true, false>(a, I.g, blockIdx.x - I.block0, nblk);
+}
+
+__global__ void __launch_bounds__(256) k_commit_batch(const EventArgs* tmpl, const BatchLaunch bl)
+{
+    int nblk;
+    const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
+    const EventArgs a = tmpl[I.rep * kMaxSpecies + I.sel];
+    commit_body<true, false>(a, I.g, blockIdx.x - I.block0, nblk);
+}
+
+__global__ void __launch_bounds__(256) k_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch bl)
+{
+    int nblk;
+    const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
+    const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
+    reconcile_body(r, blockIdx.x - I.block0, nblk);
+}
+
+__global__ void __launch_bounds__(256) k_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch bl)
+{
+    int nblk;
+    const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
+    const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
+    copyback_body(r, blockIdx.x - I.block0, nblk);
+}
+
+// one block per item
+__global__ void __launch_bounds__(1024) k_births_batch(const EventArgs* tmpl, const BatchLaunch bl)
+{
+    const BatchItem I = bl.item[blockIdx.x];
+    const EventArgs a = tmpl[I.rep * kMaxSpecies + I.sel];
+    births_body(a);
+}
+
+void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+{
+    k_claim_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+}
+
+void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+{
+    k_commit_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+}
+
+void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+{
+    k_reconcile_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+}
+
+void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+{
+    k_copyback_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+}
+
+void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+{
+    static bool configured = false;
+    const int smem = kBirthSortMax * (int)sizeof(unsigned long long);
+    if (!configured) {
+        cudaFuncSetAttribute(k_births_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = true;
+    }
+    k_births_batch<<<bl.n, 1024, smem, st>>>(tmpl, bl);
 }
 
 }  // namespace psc

@@ -1,0 +1,114 @@
+// psc_runtime.h -- host-side lattice state shared by the runtime files
+// (psc_api.cpp: single lattices; psc_batch.cpp: batches and the server).
+// Not part of the public ABI.
+#pragma once
+
+#include "psc.h"
+#include "psc_internal.h"
+
+#include <cstdint>
+#include <vector>
+
+namespace psc_rt {
+
+using namespace psc;
+
+struct Species {
+    double D = 0.0;
+    int64_t n0 = 0;
+    double tau = 0.0;
+    uint64_t done = 0;
+    int n_fo = 0;
+    int fo[kMaxFirstOrder] = {};
+};
+
+struct Reaction {
+    int nr = 0, np = 0;
+    int r[2] = {0, 0}, p[2] = {0, 0};
+    double k = 0.0;
+    double prob = 0.0;
+};
+
+}  // namespace psc_rt
+
+using namespace psc;
+
+struct psc_lattice {
+    int32_t ni = 0, nj = 0, nk = 0;
+    int64_t V = 0;
+    double rv = 0.0;
+    uint32_t bflags = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+
+    int nsp = 0;
+    psc_rt::Species sp[kMaxSpecies];
+    int nrx = 0;
+    psc_rt::Reaction rx[kMaxReactions];
+    int8_t pair[kMaxSpecies][kMaxSpecies];
+
+    bool populated = false;
+    bool clamped = false;
+    uint64_t seed = 0;
+    uint32_t g = 0;
+    double clock = 0.0;
+
+    psc::Geometry geo{};
+    ModelDev model_h{};
+    ModelDev* model_d = nullptr;
+    uint16_t* occ = nullptr;
+    uint32_t* bits = nullptr;          // vacancy mirror, one bit per voxel
+    uint32_t* claim = nullptr;         // per-voxel claim words (small lattices)
+    uint64_t* tables[2] = {nullptr, nullptr};   // claim hash tables (large lattices)
+    uint32_t table_used[2] = {0, 0};   // slots written by the event that used it
+    int64_t table_slots = 0;
+    BarrierState* barrier = nullptr;
+    uint32_t hash_bits[kMaxSpecies] = {};
+    Scalars* sc = nullptr;
+    Birth* births = nullptr;
+    int32_t births_cap = 0;
+    SpeciesList tmp{};
+    int32_t cap[kMaxSpecies] = {};
+    uint32_t* rs_keys = nullptr;      // re-sort keys / values
+    uint32_t* rs_vals = nullptr;
+    SortScratch rs_scratch;
+    int64_t rs_max = 0;
+
+    bool general[kMaxSpecies] = {};
+    bool live[kMaxSpecies] = {};       // takes part in a reaction: keeps its codes
+    bool fo2[kMaxSpecies] = {};
+    std::vector<int> reconcile[kMaxSpecies];
+    uint64_t since_resort[kMaxSpecies] = {};
+
+    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3};
+    int64_t launches = 0;
+    uint64_t events = 0;
+    uint64_t h2d = 0, d2h = 0;
+
+    // CUDA-event spans around kernels (psc_options.time_kernels)
+    struct Span { cudaEvent_t a, b; int kind; int64_t events; };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;
+    int sticky = PSC_OK;
+    std::vector<void*> allocs;
+};
+
+namespace psc_rt {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~DevGuard() { int cur = -1; cudaGetDevice(&cur); if (prev >= 0 && cur != prev) cudaSetDevice(prev); }
+};
+
+int cuda_fail(psc_lattice* L, cudaError_t e);
+void* dev_alloc(psc_lattice* L, size_t bytes);
+int event_blocks(const psc_lattice* L, int64_t work);
+EventArgs event_args(const psc_lattice* L, int s);
+ReconcileArgs reconcile_args(const psc_lattice* L, int x);
+bool next_event(const psc_lattice* L, int* s_out, double* t_out);
+int check_device(psc_lattice* L);
+
+}  // namespace psc_rt

@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -51,6 +53,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--replicas", type=int, default=512, help="replicas of the serving workload")
+    ap.add_argument("--serial-sample", type=int, default=16, help="replicas timed one at a time")
     return ap.parse_args()
 
 
@@ -300,6 +305,106 @@ def e2e_run(psc, args, rank, local, torch):
 
 
 # ---------------------------------------------------------------------------
+# batched replicas and serving: replicas of the 64^3 A + B -> C model with even
+# cubic edges uniform in 32..160, occupancy uniform in 1-20 % split between A
+# and B, seeds 5000 + r, each run to 2000 hop intervals of A (4000 events)
+# ---------------------------------------------------------------------------
+SERVE_RV = 1e-8
+SERVE_D = 1e-12
+SERVE_K = 1e-19
+SERVE_TAU = 2 * SERVE_RV * SERVE_RV / (3 * SERVE_D)
+SERVE_T_END = 2000 * SERVE_TAU
+
+
+def serving_replicas(n, seed=20261202):
+    import random
+    rnd = random.Random(seed)
+    out = []
+    for r in range(n):
+        e = 2 * rnd.randint(16, 80)
+        occ = rnd.uniform(0.01, 0.20)
+        half = int(occ * e ** 3 / 2)
+        out.append(dict(shape=(e, e, e), counts=[half, half, 0], seed=5000 + r))
+    return out
+
+
+def serving_arm(args, local):
+    import random
+    import paper_1605_03726_gb300 as psc
+
+    reps = serving_replicas(args.replicas)
+    D = [SERVE_D, SERVE_D, 0.0]
+    rx = [((0, 1), (2,), SERVE_K)]
+    attempts = lambda q: 2000 * (q["counts"][0] + q["counts"][1])   # upper bound: counts fall as C forms
+    # one at a time through the lattice API (a sample of the same replicas)
+    sample = reps[: max(1, args.serial_sample)]
+    t0 = time.perf_counter()
+    serial_counts = []
+    for q in sample:
+        L = psc.Lattice(*q["shape"], voxel_radius=SERVE_RV, device=local)
+        for d, c in zip(D, q["counts"]):
+            L.add_species(d, c)
+        L.add_reaction(*rx[0])
+        L.populate(q["seed"])
+        L.run(SERVE_T_END)
+        serial_counts.append(L.counts())
+        L.close()
+    serial_s = time.perf_counter() - t0
+    # all replicas submitted at once to the batching server
+    free, total = __import__("torch").cuda.mem_get_info(local)
+    cap = int(min(free * 0.6, 64e9))
+    S = psc.Server(max_device_bytes=cap, max_active=512, device=local)
+    t0 = time.perf_counter()
+    tickets = [S.submit(q["shape"], D, q["counts"], rx, q["seed"], SERVE_T_END) for q in reps]
+    while True:
+        a, w = S.step(64)
+        if a == 0 and w == 0:
+            break
+    batch_s = time.perf_counter() - t0
+    results = [S.result(t) for t in tickets]
+    _, peak = S.memory()
+    S.close()
+    same = all(np.array_equal(results[i][0], serial_counts[i]) for i in range(len(sample)))
+    # Poisson arrivals at 200 requests/s (seeded gaps), served as they come
+    rnd = random.Random(7)
+    arrivals, t = [], 0.0
+    for _ in reps:
+        t += rnd.expovariate(200.0)
+        arrivals.append(t)
+    S = psc.Server(max_device_bytes=cap, max_active=512, device=local)
+    t0 = time.perf_counter()
+    nxt, tk = 0, []
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(reps) and arrivals[nxt] <= now:
+            q = reps[nxt]
+            tk.append(S.submit(q["shape"], D, q["counts"], rx, q["seed"], SERVE_T_END))
+            nxt += 1
+        a, w = S.step(32)
+        if nxt == len(reps) and a == 0 and w == 0:
+            break
+        if a == 0 and w == 0:
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - now)))
+    stream_s = time.perf_counter() - t0
+    lat = sorted(S.result(t)[1] for t in tk)
+    S.close()
+    pct = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+    return {
+        "workload": "%d replicas of the A + B -> C model (64^3 case) with even edges 32-160, 1-20 %% occupancy, "
+                    "2000 hop intervals each" % len(reps),
+        "replicas_per_s_batched": round(len(reps) / batch_s, 3),
+        "replicas_per_s_serial": round(len(sample) / serial_s, 3),
+        "speedup": round((len(reps) / batch_s) / (len(sample) / serial_s), 2),
+        "serial_sample": len(sample),
+        "serial_matches_batched": bool(same),
+        "batched_attempts_per_s_upper": round(sum(attempts(q) for q in reps) / batch_s, 1),
+        "peak_device_bytes": int(peak),
+        "poisson_200_per_s": {"p50_s": round(pct(0.50), 4), "p99_s": round(pct(0.99), 4),
+                              "replicas_per_s": round(len(reps) / stream_s, 3), "makespan_s": round(stream_s, 3)},
+    }
+
+
+# ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
 def oracle_lattice(seed):
@@ -380,6 +485,8 @@ def main():
     }
     if "e2e" in res:
         out["e2e"] = res["e2e"]
+    if world == 1 and not args.no_serving:
+        out["serving"] = serving_arm(args, local)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(out))

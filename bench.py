@@ -64,6 +64,53 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+class Ranks:
+    """Host-side coordination of the job's ranks (one process per GPU, one
+    independent replica each): a barrier on both sides of the timed region and
+    the maximum over ranks of the timed duration.  Nothing on the data path
+    crosses ranks.  backend "nccl" on GPUs, "gloo" for host-only runs."""
+
+    def __init__(self, rank, world, backend="nccl", device=None):
+        self.rank, self.world, self.backend = rank, world, backend
+        self.device = device
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", device)} if backend == "nccl" else {}
+            dist.init_process_group(backend, rank=rank, world_size=world, **kw)
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return float(x)
+        import torch
+        import torch.distributed as dist
+        dev = torch.device("cuda", self.device) if self.backend == "nccl" else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+
+
+def replica_seed(rank):
+    """Seed of the replica rank `rank` runs (replicas differ, runs repeat)."""
+    return 1 + rank
+
+
+def job_throughput(units_per_rank, world, elapsed_ms_max):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (elapsed_ms_max * 1e-3)
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -170,16 +217,10 @@ def gpu_arm(args, rank, world, local):
     import paper_1605_03726_gb300 as psc
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks(rank, world, "nccl", local)
+    barrier = ranks.barrier
     stream = torch.cuda.Stream(device=local)
-    L = make_lattice(psc, 1 + rank, local, stream.cuda_stream)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    L = make_lattice(psc, replica_seed(rank), local, stream.cuda_stream)
 
     # warm-up
     for _ in range(args.warmup):
@@ -208,14 +249,8 @@ def gpu_arm(args, rank, world, local):
     launches = L.stats()["launches"] - launches0
     L.set_options(time_kernels=-1)
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-
-    attempts = args.steps * EVENTS_PER_STEP * N_MOL * world
-    value = attempts / (elapsed_ms * 1e-3)
+    elapsed_ms = ranks.max(elapsed_ms)
+    value = job_throughput(args.steps * EVENTS_PER_STEP * N_MOL, world, elapsed_ms)
 
     # success fraction of the hops, from a short counted run after the timed region
     L.set_options(collect_stats=1)
@@ -260,11 +295,8 @@ def gpu_arm(args, rank, world, local):
            "gpu_launches": int(launches)}
 
     if not args.no_e2e:
-        res["e2e"] = e2e_run(psc, args, rank, local, torch)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+        res["e2e"] = e2e_run(psc, args, rank, local, torch, ranks)
+    ranks.close()
     return res
 
 
@@ -278,16 +310,17 @@ def kernel_revision():
     return h.hexdigest()[:16]
 
 
-def e2e_run(psc, args, rank, local, torch):
+def e2e_run(psc, args, rank, local, torch, ranks):
     """The whole job through the C ABI with host buffers: create, populate,
     K steps each followed by a read of the species counts into host memory,
-    final positions read back, destroy."""
+    final positions read back, destroy.  Max over ranks of the wall time."""
     torch.cuda.synchronize(local)
+    ranks.barrier()
     t0 = time.perf_counter()
     L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=local)
     L.add_species(D, N_MOL)
     L.set_options(resort_period=RESORT_PERIOD)
-    L.populate(1 + rank)
+    L.populate(replica_seed(rank))
     for _ in range(args.steps):
         L.run_events(EVENTS_PER_STEP)
         c = L.counts()
@@ -297,7 +330,8 @@ def e2e_run(psc, args, rank, local, torch):
     t1 = time.perf_counter()
     assert int(c[0]) == N_MOL and len(ids) == N_MOL
     steps = max(1, args.steps)
-    return {"value": args.steps * EVENTS_PER_STEP * N_MOL / (t1 - t0), "unit": UNIT,
+    wall_ms = ranks.max((t1 - t0) * 1e3)
+    return {"value": job_throughput(args.steps * EVENTS_PER_STEP * N_MOL, ranks.world, wall_ms), "unit": UNIT,
             "h2d_bytes_per_step": int(st["h2d_bytes"] // steps),
             "d2h_bytes_per_step": int(st["d2h_bytes"] // steps),
             "includes": "lattice create + populate (placement sort of 134M voxels) + K steps, "

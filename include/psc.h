@@ -132,6 +132,17 @@ typedef struct {
     int32_t claim_slots;      /* before populate: hash slots per molecule of
                                  the largest mobile species, rounded up to a
                                  power of two (default 3)                      */
+    int32_t run_per_thread;   /* persistent launches: at least this many
+                                 molecules per thread (picks the launch shape;
+                                 0/-1 = fewest that fit)                       */
+    int32_t barrier_timeout_us; /* persistent launches: a block that waits
+                                 longer than this at a grid barrier gives up;
+                                 the call then fails with PSC_E_TIMEOUT and
+                                 the lattice keeps that error (default 10^6)   */
+    int32_t barrier_phantom;  /* tests of the time-out path only: arrivals the
+                                 grid barrier awaits from blocks that do not
+                                 exist, so every persistent launch waits out
+                                 barrier_timeout_us (0/-1 = none, default)     */
 } psc_options;
 
 /*
@@ -224,6 +235,37 @@ int psc_kernel_times_get(psc_lattice *L, psc_kernel_times *out);
 /* Change tunables (psc_options); allowed at any time between calls. */
 int psc_set_options(psc_lattice *L, const psc_options *opt);
 
+/*
+ * Autotuner: picks the launch options of a lattice by timing real events.
+ * It tries, one group after another keeping the best of each, the block
+ * shape of the per-event kernels (128 or 256 threads x 4, 8 or 16 blocks per
+ * SM), persistent stretches on or off with 0 (fewest that fit), 8 or 16
+ * molecules per thread, and the Morton re-sort period (16 .. 512 events or
+ * none; each of these trials starts from freshly sorted lists and spans at
+ * least two periods).  Each trial times a window of events with CUDA events
+ * on the lattice's stream.  The options change only how the work is laid
+ * out on the GPU, never the results (Sec. 2.3's synchronous rule resolves
+ * every event from its snapshot and the lowest id), so the trials are real
+ * events: the lattice advances by out->events events (at most max_events)
+ * and ends bit-identical to a run of that many events without tuning.  The
+ * chosen options stay set.  About 3000 events cover every trial; fewer
+ * events skip the re-sort periods whose windows no longer fit.
+ * Errors: PSC_E_ARG, PSC_E_ORDER (not populated), the lattice's stored error,
+ * and those of psc_run_events.
+ */
+typedef struct {
+    int32_t persistent;        /* chosen psc_options values                  */
+    int32_t run_per_thread;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t resort_period;     /* -1 = no re-sort                            */
+    int32_t trials;            /* configurations timed                       */
+    int64_t events;            /* events the trials ran                      */
+    double  us_per_event;      /* of the chosen configuration                */
+    double  us_per_event_before; /* of the options in force at the call       */
+} psc_tune_result;
+int psc_autotune(psc_lattice *L, int64_t max_events, psc_tune_result *out);
+
 /* Hop interval of a species and p_AB of a second-order reaction as the engine
    computes them (Sec. 2.3 Eq. 3, Sec. 2.4.2 Eq. 6; p_AB before clamping). */
 double psc_tau(const psc_lattice *L, int32_t species);
@@ -273,6 +315,22 @@ int  psc_batch_run_events(psc_batch *B, int64_t n_events);
 int  psc_batch_run(psc_batch *B, double t_end);
 int64_t psc_batch_launches(const psc_batch *B);
 void psc_batch_destroy(psc_batch *B);
+
+/* Batch autotuner: threads per block (128, 256) and the most blocks one
+   member's event gets in a batched launch (8 .. 256, the rest grid-strided),
+   chosen by timing windows of batched events (CUDA events on the batch's
+   stream).  Trial rounds are real events of every member (results are the
+   same under any block shape); at most max_rounds batched events run.  The
+   chosen shape stays set for the batch.  Errors: PSC_E_ARG, PSC_E_CUDA. */
+typedef struct {
+    int32_t threads;
+    int32_t blocks_per_member;
+    int32_t trials;
+    int64_t rounds;            /* batched events the trials ran              */
+    double  us_per_round;      /* of the chosen shape                        */
+    double  us_per_round_before;
+} psc_batch_tune_result;
+int psc_batch_autotune(psc_batch *B, int64_t max_rounds, psc_batch_tune_result *out);
 
 /*
  * Serving: a request loop with continuous batching.  A request describes a

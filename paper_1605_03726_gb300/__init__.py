@@ -34,7 +34,7 @@ class Stats(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
-        "claim_table", "persistent", "slot_map", "claim_slots")]
+        "claim_table", "persistent", "slot_map", "claim_slots", "run_per_thread", "barrier_timeout_us", "barrier_phantom")]
 
 
 class KernelTimes(ctypes.Structure):
@@ -43,6 +43,27 @@ class KernelTimes(ctypes.Structure):
                 ("claim_launches", ctypes.c_int64), ("commit_launches", ctypes.c_int64),
                 ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64),
                 ("run_ms", ctypes.c_double), ("run_launches", ctypes.c_int64), ("run_events", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))
+                for n, t in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("run_per_thread", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("resort_period", ctypes.c_int32), ("trials", ctypes.c_int32), ("events", ctypes.c_int64),
+                ("us_per_event", ctypes.c_double), ("us_per_event_before", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))
+                for n, t in self._fields_}
+
+
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("blocks_per_member", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("rounds", ctypes.c_int64), ("us_per_round", ctypes.c_double),
+                ("us_per_round_before", ctypes.c_double)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))
@@ -90,6 +111,8 @@ def lib():
             "psc_stats_get": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
             "psc_set_options": (ctypes.c_int, [P, ctypes.POINTER(Options)]),
             "psc_kernel_times_get": (ctypes.c_int, [P, ctypes.POINTER(KernelTimes)]),
+            "psc_autotune": (ctypes.c_int, [P, i64, ctypes.POINTER(TuneResult)]),
+            "psc_batch_autotune": (ctypes.c_int, [P, i64, ctypes.POINTER(BatchTuneResult)]),
             "psc_tau": (dbl, [P, i32]),
             "psc_p_ab": (dbl, [P, i32]),
             "psc_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
@@ -123,7 +146,7 @@ def lib():
 EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_populate", "psc_run",
             "psc_run_events", "psc_synchronize", "psc_counts", "psc_coords", "psc_unwrapped", "psc_grid",
             "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_kernel_times_get",
-            "psc_tau", "psc_p_ab",
+            "psc_autotune", "psc_batch_autotune", "psc_tau", "psc_p_ab",
             "psc_device_bytes", "psc_lattice_destroy", "psc_status_string", "psc_set_allocator",
             "psc_hop_events_static", "psc_batch_create", "psc_batch_add", "psc_batch_remove", "psc_batch_size",
             "psc_batch_run_events", "psc_batch_run", "psc_batch_launches", "psc_batch_destroy",
@@ -281,6 +304,12 @@ class Lattice:
         _check("psc_kernel_times_get", lib().psc_kernel_times_get(self._h, ctypes.byref(k)))
         return k.as_dict()
 
+    def autotune(self, max_events=3000):
+        """Pick launch options by timing real events (psc_autotune); returns the choice."""
+        r = TuneResult()
+        _check("psc_autotune", lib().psc_autotune(self._h, int(max_events), ctypes.byref(r)))
+        return r.as_dict()
+
     def tau(self, species):
         return lib().psc_tau(self._h, species)
 
@@ -318,6 +347,12 @@ class Batch:
 
     def launches(self):
         return int(lib().psc_batch_launches(self._h))
+
+    def autotune(self, max_rounds=200):
+        """Pick the batched launches' block shape by timing real batched events."""
+        r = BatchTuneResult()
+        _check("psc_batch_autotune", lib().psc_batch_autotune(self._h, int(max_rounds), ctypes.byref(r)))
+        return r.as_dict()
 
     def close(self):
         if self._h:

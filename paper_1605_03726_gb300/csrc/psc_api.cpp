@@ -234,7 +234,7 @@ int run_width(const psc_lattice* L, int s, int* threads, int* blocks)
 {
     if (L->opt.persistent <= 0 || L->general[s]) return 0;
     if (L->tables[0] && L->hash_bits[s] > 27) return 0;
-    return run_capacity(L->cap[s], threads, blocks, L->sm_count);
+    return run_capacity(L->cap[s], threads, blocks, L->sm_count, L->opt.run_per_thread);
 }
 
 int enqueue_run(psc_lattice* L, int s, int n_events, int per_thread, int threads, int blocks)
@@ -254,6 +254,8 @@ int enqueue_run(psc_lattice* L, int s, int n_events, int per_thread, int threads
     r.tables[1] = L->tables[1];
     r.n_events = n_events;
     r.barrier = L->barrier;
+    r.barrier_timeout_ns = (uint64_t)L->opt.barrier_timeout_us * 1000ull;
+    r.barrier_phantom = (uint32_t)L->opt.barrier_phantom;
     int rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st));
     if (rc) return rc;
     cudaEvent_t sp = span_open(L);
@@ -290,7 +292,8 @@ int check_device(psc_lattice* L)
     e = cudaMemcpy(&err, &L->sc->err, sizeof(err), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(L, e);
     L->d2h += sizeof(err);
-    if (err) L->sticky = PSC_E_CAPACITY;
+    if (err & kErrBarrierTimeout) L->sticky = PSC_E_TIMEOUT;
+    else if (err) L->sticky = PSC_E_CAPACITY;
     return L->sticky;
 }
 
@@ -623,10 +626,14 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     return L->clamped ? PSC_W_PCLAMP : PSC_OK;
 }
 
+}  // extern "C"
+
+namespace psc_rt {
+
 // Queue events in scheduler order until max_events are queued or the next
 // event lies after t_end.  Consecutive events of one species without
 // reactions are grouped into persistent stretches (cut at re-sort points).
-static int drive(psc_lattice* L, double t_end, int64_t max_events)
+int drive(psc_lattice* L, double t_end, int64_t max_events)
 {
     int64_t queued = 0;
     while (queued < max_events) {
@@ -679,6 +686,10 @@ static int drive(psc_lattice* L, double t_end, int64_t max_events)
     }
     return PSC_OK;
 }
+
+}  // namespace psc_rt
+
+extern "C" {
 
 int psc_run(psc_lattice* L, double t_end)
 {
@@ -885,6 +896,12 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
         L->opt.claim_table = o->claim_table;
     }
     if (o->persistent) L->opt.persistent = o->persistent;
+    if (o->run_per_thread) L->opt.run_per_thread = o->run_per_thread < 0 ? 0 : o->run_per_thread;
+    if (o->barrier_timeout_us) {
+        if (o->barrier_timeout_us < 0) return PSC_E_ARG;
+        L->opt.barrier_timeout_us = o->barrier_timeout_us;
+    }
+    if (o->barrier_phantom) L->opt.barrier_phantom = o->barrier_phantom < 0 ? 0 : o->barrier_phantom;
     if (o->slot_map) {
         if (o->slot_map < 1 || o->slot_map > 3) return PSC_E_ARG;
         L->opt.slot_map = o->slot_map;

@@ -20,7 +20,8 @@ using namespace psc_rt;
 
 namespace {
 
-constexpr int kItemBlocksMax = 64;        // blocks per member per launch (grid-stride inside)
+constexpr int kItemBlocksMaxDefault = 64;   // blocks per member per launch (grid-stride inside)
+constexpr int kItemThreadsDefault = 256;   // threads per block of the batched launches
 
 struct Member {
     psc_lattice* L = nullptr;
@@ -38,14 +39,16 @@ struct psc_batch {
     EventArgs* tmpl_ev = nullptr;         // [kBatchMax][kMaxSpecies] on the device
     ReconcileArgs* tmpl_rc = nullptr;
     int64_t launches = 0;
+    int threads = kItemThreadsDefault;
+    int item_blocks_max = kItemBlocksMaxDefault;
 };
 
 namespace {
 
-int item_blocks(int64_t work)
+int item_blocks(const psc_batch* B, int64_t work)
 {
-    const int64_t b = (work + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kItemBlocksMax));
+    const int64_t b = (work + B->threads - 1) / B->threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, B->item_blocks_max));
 }
 
 // Queue the next event of every member whose next event time is <= its
@@ -74,12 +77,12 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
         it.sel = s;
         it.g = L->g;
         it.block0 = total;
-        total += item_blocks(L->cap[s]);
+        total += item_blocks(B, L->cap[s]);
     }
     if (na == 0) return 0;
     bl.total_blocks = total;
-    launch_claim_batch(B->tmpl_ev, bl, B->stream);
-    launch_commit_batch(B->tmpl_ev, bl, B->stream);
+    launch_claim_batch(B->tmpl_ev, bl, B->threads, B->stream);
+    launch_commit_batch(B->tmpl_ev, bl, B->threads, B->stream);
     B->launches += 2;
     // list passes: the k-th list each member's event touches
     for (int k = 0;; ++k) {
@@ -94,12 +97,12 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
             it.sel = rec[k];
             it.g = 0;
             it.block0 = total;
-            total += item_blocks(L->cap[rec[k]]);
+            total += item_blocks(B, L->cap[rec[k]]);
         }
         if (bl.n == 0) break;
         bl.total_blocks = total;
-        launch_reconcile_batch(B->tmpl_rc, bl, B->stream);
-        launch_copyback_batch(B->tmpl_rc, bl, B->stream);
+        launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
+        launch_copyback_batch(B->tmpl_rc, bl, B->threads, B->stream);
         B->launches += 2;
     }
     bl.n = 0;
@@ -254,6 +257,70 @@ int psc_batch_run(psc_batch* B, double t_end)
         if (L && t_end > L->clock) L->clock = t_end;
     }
     return PSC_OK;
+}
+
+// Block shape of the batched launches, tuned by timing batched events.  Like
+// the lattice tuner it changes only how work is laid out on the GPU, so the
+// trial rounds are real events of every member.
+int psc_batch_autotune(psc_batch* B, int64_t max_rounds, psc_batch_tune_result* out)
+{
+    if (!B || !out || max_rounds < 0) return PSC_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    DevGuard dg(B->device);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return PSC_E_CUDA;
+    }
+    const int64_t W = std::max<int64_t>(2, std::min<int64_t>(64, max_rounds / 14));
+    int64_t budget = max_rounds;
+    int rc = PSC_OK;
+    // run up to n batched events; *us = microseconds per batched event (timed)
+    auto rounds = [&](int64_t n, bool time_it, double* us) -> int {
+        n = std::min(n, budget);
+        int64_t done = 0;
+        if (time_it && cudaEventRecord(a, B->stream) != cudaSuccess) return PSC_E_CUDA;
+        for (; done < n; ++done) {
+            int r;
+            if (batch_event(B, INFINITY, &r) == 0) break;
+            if (r) return r;
+        }
+        budget -= done;
+        out->rounds += done;
+        if (!time_it) return PSC_OK;
+        if (cudaEventRecord(b, B->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
+            return PSC_E_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return PSC_E_CUDA;
+        out->trials++;
+        *us = done > 0 ? 1e3 * (double)ms / (double)done : INFINITY;
+        return PSC_OK;
+    };
+    int best_t = B->threads, best_m = B->item_blocks_max;
+    double best_us = INFINITY;
+    rc = rounds(1, false, nullptr);
+    if (!rc) rc = rounds(W, true, &best_us);
+    out->us_per_round_before = best_us;
+    const int threads[] = {128, 256};
+    const int per_member[] = {8, 16, 32, 64, 128, 256};
+    for (int th : threads) {
+        for (int m : per_member) {
+            if (rc || budget <= 0) break;
+            if (th == best_t && m == best_m) continue;
+            B->threads = th;
+            B->item_blocks_max = m;
+            double us;
+            if (!(rc = rounds(W, true, &us)) && us < best_us) { best_us = us; best_t = th; best_m = m; }
+        }
+    }
+    B->threads = best_t;
+    B->item_blocks_max = best_m;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    out->threads = best_t;
+    out->blocks_per_member = best_m;
+    out->us_per_round = best_us;
+    return rc;
 }
 
 void psc_batch_destroy(psc_batch* B)

@@ -151,6 +151,8 @@ struct RunArgs {
     uint64_t* tables[2];       // claim tables, alternating by event parity
     int32_t n_events;
     BarrierState* barrier;
+    uint64_t barrier_timeout_ns;  // a block gives up waiting at a barrier after this long
+    uint32_t barrier_phantom;     // arrivals awaited from blocks that do not exist (0; tests only)
 };
 
 struct ReconcileArgs {
@@ -171,7 +173,7 @@ void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cu
 void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st);
 // Molecules per thread the persistent kernel holds in registers (0 = the
 // stretch does not fit); threads = its launch width.
-int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count);
+int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count, int min_per_thread);
 cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st);
 void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
                         int64_t V, int blocks, cudaStream_t st);
@@ -213,10 +215,10 @@ struct BatchLaunch {
     int32_t total_blocks;
     BatchItem item[kBatchMax];
 };
-void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
-void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
-void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
-void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
+void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
+void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
+void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
+void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
 void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
 
 // ---- radix sort (psc_sort.cu) ----

@@ -573,7 +573,7 @@ void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cu
 // that one slot, and the next event's claim phase empties it again (the
 // tables alternate, so the table being emptied is not in use).
 // ---------------------------------------------------------------------------
-constexpr uint64_t kBarrierTimeoutNs = 1000000000ull;   // 1 s
+constexpr unsigned int kBarrierMaxSpins = 1u << 28;
 constexpr int kGroup = 1;                                  // molecules in flight per thread
 
 __device__ __forceinline__ uint64_t globaltimer_ns()
@@ -585,14 +585,18 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 
 // Grid barrier: block 0 adds 2^31 - (blocks - 1), every other block adds 1,
 // so the top bit of the arrival word flips exactly when all have arrived.
-// The wait is bounded (about one second of wall time): on time-out the block
-// raises kErrBarrierTimeout and every thread of it returns false.
-__device__ __forceinline__ bool grid_barrier(BarrierState* bs, int32_t* err)
+// The wait is bounded by timeout_ns of wall time (one second unless the
+// caller sets it) and by a spin count: on time-out the block raises
+// kErrBarrierTimeout and every thread of it returns false.  `phantom` counts
+// arrivals awaited from blocks that do not exist (0 outside tests): with
+// phantom > 0 the bit never flips and every block waits out its bound.
+__device__ __forceinline__ bool grid_barrier(BarrierState* bs, int32_t* err, uint64_t timeout_ns,
+                                             uint32_t phantom)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u + phantom) : 1u;
         __threadfence();
         const unsigned int old = atomicAdd(&bs->arrive, inc);
         volatile unsigned int* word = &bs->arrive;
@@ -602,7 +606,8 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, int32_t* err)
             if ((spins & 1023u) == 0u) {
                 const uint64_t now = globaltimer_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > kBarrierTimeoutNs) {
+                // the spin count bounds the wait even if the timer were to stall
+                if (now - t0 > timeout_ns || spins >= kBarrierMaxSpins) {
                     atomicOr(err, kErrBarrierTimeout);
                     good = 0;
                     break;
@@ -720,7 +725,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_hop_run(const RunArgs r)
             for (int x = 0; x < kGroup; ++x)
                 if (m0 + x < mine) s_st[(m0 + x) * THREADS + threadIdx.x] = stg[x];
         }
-        if (!grid_barrier(r.barrier, &a.sc->err)) return;
+        if (!grid_barrier(r.barrier, &a.sc->err, r.barrier_timeout_ns, r.barrier_phantom)) return;
         // ---- commit phase: slot reads of a group in flight together ----
         for (int m0 = 0; m0 < mine; m0 += kGroup) {
             uint32_t stg[kGroup], cw[kGroup];
@@ -766,7 +771,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_hop_run(const RunArgs r)
                 ++n_hop;
             }
         }
-        if (!grid_barrier(r.barrier, &a.sc->err)) return;
+        if (!grid_barrier(r.barrier, &a.sc->err, r.barrier_timeout_ns, r.barrier_phantom)) return;
     }
     // leave both tables empty: the last event's slots (the one before was
     // emptied during the last claim phase)
@@ -795,11 +800,11 @@ struct RunShape {
 static const RunShape kRunShapes[] = {
     {2, 768, 2}, {4, 768, 2}, {6, 768, 2}, {8, 768, 1}, {12, 768, 1}, {16, 768, 1}, {24, 768, 1}};
 
-int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count)
+int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count, int min_per_thread)
 {
     for (const RunShape& sh : kRunShapes) {
         const int64_t T = (int64_t)sh.threads * sh.blocks_per_sm * sm_count;
-        if (n <= (int64_t)sh.per_thread * T) {
+        if (sh.per_thread >= min_per_thread && n <= (int64_t)sh.per_thread * T) {
             *threads_per_block = sh.threads;
             *blocks = sh.blocks_per_sm * sm_count;
             return sh.per_thread;
@@ -1239,24 +1244,24 @@ __global__ void __launch_bounds__(1024) k_births_batch(const EventArgs* tmpl, co
     births_body(a);
 }
 
-void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st)
 {
-    k_claim_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+    k_claim_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
 }
 
-void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st)
 {
-    k_commit_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+    k_commit_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
 }
 
-void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st)
 {
-    k_reconcile_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+    k_reconcile_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
 }
 
-void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
+void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st)
 {
-    k_copyback_batch<<<bl.total_blocks, 256, 0, st>>>(tmpl, bl);
+    k_copyback_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
 }
 
 void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)

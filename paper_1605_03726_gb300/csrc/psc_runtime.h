@@ -82,7 +82,7 @@ struct psc_lattice {
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3};
+    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3, 0, 1000000, 0};
     int64_t launches = 0;
     uint64_t events = 0;
     uint64_t h2d = 0, d2h = 0;
@@ -110,5 +110,9 @@ EventArgs event_args(const psc_lattice* L, int s);
 ReconcileArgs reconcile_args(const psc_lattice* L, int x);
 bool next_event(const psc_lattice* L, int* s_out, double* t_out);
 int check_device(psc_lattice* L);
+// queue events in scheduler order until max_events or the next event lies after t_end
+int drive(psc_lattice* L, double t_end, int64_t max_events);
+// Morton re-sort of species s's list (queued on the lattice's stream)
+int resort(psc_lattice* L, int s);
 
 }  // namespace psc_rt

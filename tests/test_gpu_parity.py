@@ -216,9 +216,11 @@ def test_diffusion_256cubed_one_percent(persistent):
 @pytest.mark.slow
 def test_diffusion_512cubed_full_size():
     # the 512^3 lattice at 1 % occupancy (1,342,177 molecules, D = 10 um^2/s) in
-    # the launch configuration the benchmark times
+    # the launch configuration the benchmark times: one persistent stretch of
+    # 100 events, the re-sort, then part of the next stretch
     n = int(0.01 * 512 ** 3)
     g, o = build_both((512, 512, 512), lambda L: models.diffusion_only(L, n, D=10e-12), 1, resort_period=100)
-    g.run_events(3)
-    o.run_events(3)
-    assert_same(g, o)
+    for chunk in (3, 97, 40):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)

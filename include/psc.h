@@ -143,6 +143,12 @@ typedef struct {
                                  grid barrier awaits from blocks that do not
                                  exist, so every persistent launch waits out
                                  barrier_timeout_us (0/-1 = none, default)     */
+    int32_t tiles;            /* persistent stretches of a species without
+                                 reactions: 1 = owner-computes tile kernel
+                                 wherever it applies, -1 = never, 0 = default
+                                 (when the species has >= 2^20 molecules)      */
+    int32_t tile_regions;     /* tile kernel: most boxes (blocks) to cut the
+                                 lattice into (0/-1 = one per SM)              */
 } psc_options;
 
 /*
@@ -239,8 +245,9 @@ int psc_set_options(psc_lattice *L, const psc_options *opt);
  * Autotuner: picks the launch options of a lattice by timing real events.
  * It tries, one group after another keeping the best of each, the block
  * shape of the per-event kernels (128 or 256 threads x 4, 8 or 16 blocks per
- * SM), persistent stretches on or off with 0 (fewest that fit), 8 or 16
- * molecules per thread, and the Morton re-sort period (16 .. 512 events or
+ * SM), persistent stretches under the tile kernel, under the molecule-list
+ * kernel with 0 (fewest that fit), 8 or 16 molecules per thread, or off, and
+ * the Morton re-sort period (16 .. 512 events or
  * none; each of these trials starts from freshly sorted lists and spans at
  * least two periods).  Each trial times a window of events with CUDA events
  * on the lattice's stream.  The options change only how the work is laid
@@ -259,6 +266,7 @@ typedef struct {
     int32_t block_threads;
     int32_t blocks_per_sm;
     int32_t resort_period;     /* -1 = no re-sort                            */
+    int32_t tiles;             /* 1 tile kernel, -1 molecule-list kernel     */
     int32_t trials;            /* configurations timed                       */
     int64_t events;            /* events the trials ran                      */
     double  us_per_event;      /* of the chosen configuration                */

@@ -34,7 +34,8 @@ class Stats(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
-        "claim_table", "persistent", "slot_map", "claim_slots", "run_per_thread", "barrier_timeout_us", "barrier_phantom")]
+        "claim_table", "persistent", "slot_map", "claim_slots", "run_per_thread", "barrier_timeout_us", "barrier_phantom", "tiles",
+        "tile_regions")]
 
 
 class KernelTimes(ctypes.Structure):
@@ -52,7 +53,8 @@ class KernelTimes(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int32), ("run_per_thread", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("resort_period", ctypes.c_int32), ("trials", ctypes.c_int32), ("events", ctypes.c_int64),
+                ("resort_period", ctypes.c_int32), ("tiles", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("events", ctypes.c_int64),
                 ("us_per_event", ctypes.c_double), ("us_per_event_before", ctypes.c_double)]
 
     def as_dict(self):

@@ -267,6 +267,152 @@ int enqueue_run(psc_lattice* L, int s, int n_events, int per_thread, int threads
     return PSC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// tile kernel (owner-computes stretches)
+// ---------------------------------------------------------------------------
+bool tile_plan(psc_lattice* L, int s, TilePlan* P)
+{
+    if (L->opt.tiles < 0 || L->general[s] || L->live[s] || !(L->sp[s].D > 0.0)) return false;
+    if (L->opt.tiles == 0 && L->sp[s].n0 < ((int64_t)1 << 20)) return false;
+    if (L->sp[s].n0 <= 0) return false;
+    // periodic axes must wrap whole bricks
+    if ((L->bflags & PSC_PERIODIC_I) && (L->ni & 3)) return false;
+    if ((L->bflags & PSC_PERIODIC_J) && (L->nj & 3)) return false;
+    if ((L->bflags & PSC_PERIODIC_K) && (L->nk & 1)) return false;
+    if (L->tables[0] && L->hash_bits[s] > 26) return false;
+    if (L->tile_smem < 0) L->tile_smem = tile_smem_limit(L->device);
+    const int nbi = (L->ni + 3) / 4, nbj = (L->nj + 3) / 4, nbk = (L->nk + 1) / 2;
+    int S = L->sm_count;
+    if (L->opt.tile_regions > 0) S = std::min(S, L->opt.tile_regions);
+    // the cut that minimises the largest box (work of the slowest block), then
+    // the halo
+    int64_t best_work = -1, best_box = 0;
+    TilePlan best{};
+    // owner tables, neighbourhood masks, outbox
+    const int64_t owners = ((nbi + nbj + nbk + 15) & ~15) + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4;
+    for (int pi = 1; pi <= std::min(std::min(nbi, S), 255); ++pi) {
+        for (int pj = 1; pj <= std::min(std::min(nbj, S / pi), 255); ++pj) {
+            for (int pk = 1; pk <= std::min(std::min(nbk, S / (pi * pj)), 255); ++pk) {
+                const int ei = (nbi + pi - 1) / pi, ej = (nbj + pj - 1) / pj, ek = (nbk + pk - 1) / pk;
+                const int64_t box = (int64_t)(ei + 2) * (ej + 2) * (ek + 2);
+                if (((box + 3) & ~3) * 4 + owners > L->tile_smem) continue;
+                if (ei > 512 || ej > 512 || ek > 512) continue;   // packed region coordinates
+                const int64_t work = (int64_t)ei * ej * ek;
+                if (best_work < 0 || work < best_work || (work == best_work && box < best_box)) {
+                    best_work = work;
+                    best_box = box;
+                    best = TilePlan{pi, pj, pk, nbi, nbj, nbk, ei, ej, ek, pi * pj * pk, (int32_t)box, 0};
+                }
+            }
+        }
+    }
+    if (best_work < 0) return false;
+    const double share = (double)best_work / ((double)nbi * nbj * nbk);
+    const int64_t cap = std::min<int64_t>(best_work * 32, (int64_t)(2.0 * share * (double)L->sp[s].n0) + 8192);
+    if (cap > INT32_MAX / 2) return false;
+    best.cap = (int32_t)cap;
+    *P = best;
+    return true;
+}
+
+static int tile_buffers(psc_lattice* L, const TilePlan& P, int64_t ids)
+{
+    auto& T = L->tile;
+    const int64_t slots = (int64_t)P.regions * P.cap;
+    if (slots > T.slots || P.regions > T.regions) {
+        for (void* p : {(void*)T.b_vox[0], (void*)T.b_vox[1], (void*)T.b_ids[0], (void*)T.b_ids[1],
+                        (void*)T.b_state, (void*)T.b_cnt, (void*)T.in_vox, (void*)T.in_ids, (void*)T.in_cnt,
+                        (void*)T.done})
+            if (p) dev_free_one(L, p);
+        const int64_t ns = std::max(slots, T.slots);
+        const int32_t nr = std::max(P.regions, T.regions);
+        for (int x = 0; x < 2; ++x) {
+            T.b_vox[x] = (int32_t*)dev_alloc(L, (size_t)ns * 4);
+            T.b_ids[x] = (uint32_t*)dev_alloc(L, (size_t)ns * 4);
+        }
+        T.b_state = (uint32_t*)dev_alloc(L, (size_t)ns * 4);
+        T.in_vox = (int32_t*)dev_alloc(L, (size_t)ns * 4);
+        T.in_ids = (uint32_t*)dev_alloc(L, (size_t)ns * 4);
+        T.b_cnt = (int32_t*)dev_alloc(L, (size_t)nr * 4);
+        T.in_cnt = (int32_t*)dev_alloc(L, (size_t)nr * 4);
+        T.done = (uint32_t*)dev_alloc(L, (size_t)nr * 4);
+        T.slots = ns;
+        T.regions = nr;
+        if (!T.b_vox[0] || !T.b_vox[1] || !T.b_ids[0] || !T.b_ids[1] || !T.b_state || !T.in_vox || !T.in_ids ||
+            !T.b_cnt || !T.in_cnt || !T.done) {
+            T.slots = 0;
+            return PSC_E_NOMEM;
+        }
+    }
+    if (ids > T.ids) {
+        if (T.img_id) dev_free_one(L, T.img_id);
+        T.img_id = (uint64_t*)dev_alloc(L, (size_t)ids * 8);
+        T.ids = T.img_id ? ids : 0;
+        if (!T.img_id) return PSC_E_NOMEM;
+    }
+    return PSC_OK;
+}
+
+int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
+{
+    cudaStream_t st = L->stream;
+    int64_t id_lo = 0;
+    for (int q = 0; q < s; ++q) id_lo += L->sp[q].n0;
+    int rc = tile_buffers(L, P, L->sp[s].n0);
+    if (rc) return rc;
+    // the one claim table must start empty
+    for (int t = 0; t < 2; ++t) {
+        if (L->tables[t] && L->table_used[t]) {
+            launch_fill_u64(L->tables[t], kEmptySlot, L->table_used[t], L->sm_count * 4, st);
+            L->table_used[t] = 0;
+            L->launches += 1;
+        }
+    }
+    TileArgs A{};
+    A.ev = event_args(L, s);
+    A.ev.ct.hash = nullptr;
+    A.ev.ct.clear = nullptr;
+    A.ev.ct.clear_n = 0;
+    A.tables[0] = L->tables[0];
+    A.tables[1] = L->tables[1];
+    A.done = L->tile.done;
+    // neighbour waits between events need boxes at least two bricks thick
+    // (then everything an event reads from outside its box was written by
+    // adjacent boxes)
+    A.nbr_sync = (P.nbi / P.pi >= 2 && P.nbj / P.pj >= 2 && P.nbk / P.pk >= 2) ? 1 : 0;
+    A.plan = P;
+    for (int x = 0; x < 2; ++x) {
+        A.b_vox[x] = L->tile.b_vox[x];
+        A.b_ids[x] = L->tile.b_ids[x];
+    }
+    A.b_state = L->tile.b_state;
+    A.b_cnt = L->tile.b_cnt;
+    A.in_vox = L->tile.in_vox;
+    A.in_ids = L->tile.in_ids;
+    A.in_cnt = L->tile.in_cnt;
+    A.img_id = L->tile.img_id;
+    A.id_lo = (uint32_t)id_lo;
+    A.n_events = (int32_t)n_events;
+    A.barrier = L->barrier;
+    A.barrier_timeout_ns = (uint64_t)L->opt.barrier_timeout_us * 1000ull;
+    A.barrier_phantom = (uint32_t)L->opt.barrier_phantom;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.b_cnt, 0, (size_t)P.regions * 4, st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.in_cnt, 0, (size_t)P.regions * 4, st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.done, 0, (size_t)P.regions * 4, st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st)))) return rc;
+    cudaEvent_t sp = span_open(L);
+    const int64_t n = L->sp[s].n0;
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 8191) / 8192, 2 * L->sm_count));
+    launch_tile_scatter(A, sblocks, st);
+    rc = cuda_fail(L, launch_tile_run(A, st));
+    if (!rc) launch_tile_gather(A, st);
+    span_close(L, sp, kSpanRun, n_events);
+    if (rc) return rc;
+    L->launches += 3;
+    L->events += (uint64_t)n_events;
+    return cuda_fail(L, cudaPeekAtLastError());
+}
+
 // Sec. 2.2: the next event belongs to the mobile species whose next diffusion
 // time (events done + 1) * tau is earliest; ties go to the lower index.
 bool next_event(const psc_lattice* L, int* s_out, double* t_out)
@@ -643,12 +789,16 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
         if (L->g == UINT32_MAX) return PSC_E_LIMIT;
         int threads = 0, blocks = 0;
         const int per = run_width(L, s, &threads, &blocks);
+        TilePlan plan{};
+        const bool tiles = per > 0 && tile_plan(L, s, &plan);
         if (per > 0) {
-            // how long does species s stay next?
+            // how long does species s stay next?  (Tile stretches keep their
+            // own spatial order: no re-sort points.)
             const uint32_t g0 = L->g;
             int64_t limit = max_events - queued;
-            if (L->opt.resort_period > 0)
+            if (L->opt.resort_period > 0 && !tiles)
                 limit = std::min<int64_t>(limit, (int64_t)L->opt.resort_period - (int64_t)L->since_resort[s]);
+            if (tiles) limit = std::min<int64_t>(limit, (int64_t)1 << 16);   // bounded launch length
             limit = std::max<int64_t>(1, std::min<int64_t>(limit, (int64_t)UINT32_MAX - L->g));
             int64_t e = 0;
             for (;;) {
@@ -663,10 +813,11 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
                 t = t2;
             }
             L->g = g0;                                   // event_args reads the first index
-            int rc = enqueue_run(L, s, (int)e, per, threads, blocks);
+            int rc = tiles ? enqueue_tiles(L, s, e, plan) : enqueue_run(L, s, (int)e, per, threads, blocks);
             L->g = g0 + (uint32_t)e;
             if (rc) return rc;
             queued += e;
+            if (tiles) continue;
             L->since_resort[s] += (uint64_t)e;
             if (L->opt.resort_period > 0 && L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
                 L->since_resort[s] = 0;
@@ -902,6 +1053,8 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
         L->opt.barrier_timeout_us = o->barrier_timeout_us;
     }
     if (o->barrier_phantom) L->opt.barrier_phantom = o->barrier_phantom < 0 ? 0 : o->barrier_phantom;
+    if (o->tiles) L->opt.tiles = o->tiles > 0 ? 1 : -1;
+    if (o->tile_regions) L->opt.tile_regions = o->tile_regions < 0 ? 0 : o->tile_regions;
     if (o->slot_map) {
         if (o->slot_map < 1 || o->slot_map > 3) return PSC_E_ARG;
         L->opt.slot_map = o->slot_map;

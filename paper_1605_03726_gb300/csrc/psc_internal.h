@@ -155,6 +155,45 @@ struct RunArgs {
     uint32_t barrier_phantom;     // arrivals awaited from blocks that do not exist (0; tests only)
 };
 
+// Owner-computes decomposition of a stretch (tile kernel): the mirror's brick
+// grid (nbi x nbj x nbk words) is cut into pi x pj x pk boxes of whole bricks,
+// one per block; region a along an axis of nb bricks spans bricks
+// [a nb / p, (a + 1) nb / p).
+struct TilePlan {
+    int32_t pi, pj, pk;
+    int32_t nbi, nbj, nbk;
+    int32_t ei, ej, ek;        // largest region extent in bricks
+    int32_t regions;
+    int32_t box_words;         // (ei + 2)(ej + 2)(ek + 2): region plus one brick of halo
+    int32_t cap;               // molecule slots per region (bucket, inbox)
+};
+
+// A stretch of a species without reactions under the tile kernel.  Each
+// region's molecules live in its bucket; a molecule that hops into another
+// region is appended to that region's inbox and joins its bucket at the next
+// event.  Wrap counters are kept by id (the species' ids are id_lo .. id_lo +
+// n - 1: it never reacts, so they are the ones populate gave it).
+struct TileArgs {
+    EventArgs ev;              // g = index of the first event
+    TilePlan plan;
+    uint64_t* tables[2];       // claim tables (hash mode), by event parity; null: per-voxel words
+    uint32_t* done;            // [regions] events whose commit phase the region has finished
+    int32_t nbr_sync;          // 1: between events wait for the neighbouring boxes only
+    int32_t* b_vox[2];         // [regions][cap] voxel of each molecule; event e
+    uint32_t* b_ids[2];        // reads buffer e & 1 and keeps its survivors in the other
+    uint32_t* b_state;         // claim-phase decision of each bucket slot
+    int32_t* b_cnt;            // [regions]
+    int32_t* in_vox;           // [regions][cap] arrivals of the last event
+    uint32_t* in_ids;
+    int32_t* in_cnt;           // [regions]
+    uint64_t* img_id;          // wrap counters by id - id_lo
+    uint32_t id_lo;
+    int32_t n_events;
+    BarrierState* barrier;
+    uint64_t barrier_timeout_ns;
+    uint32_t barrier_phantom;
+};
+
 struct ReconcileArgs {
     Geometry geo;
     uint16_t* occ;
@@ -175,6 +214,21 @@ void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStre
 // stretch does not fit); threads = its launch width.
 int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count, int min_per_thread);
 cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st);
+// tile kernel: dynamic shared memory a block may use, its need for a plan,
+// the three launches of a stretch (list -> buckets, the persistent events,
+// buckets -> list)
+int tile_smem_limit(int device);
+constexpr int kTileOutbox = 2048;           // departures a block stages per event
+constexpr int kTileQueue = 2048;            // molecules a block defers per phase (contested, leaving)
+inline int tile_smem_bytes(const TilePlan& P)
+{
+    return ((P.box_words + 3) & ~3) * 4 + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
+           ((P.nbi + P.nbj + P.nbk + 15) & ~15);
+}
+constexpr int kTileThreads = 1024;
+void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st);
+cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st);
+void launch_tile_gather(const TileArgs& A, cudaStream_t st);
 void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
                         int64_t V, int blocks, cudaStream_t st);
 void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,

@@ -25,6 +25,7 @@
 #include "psc_internal.h"
 
 #include <algorithm>
+#include <climits>
 
 namespace psc {
 
@@ -1274,5 +1275,7 @@ void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStrea
     }
     k_births_batch<<<bl.n, 1024, smem, st>>>(tmpl, bl);
 }
+
+#include "psc_tiles.cuh"
 
 }  // namespace psc

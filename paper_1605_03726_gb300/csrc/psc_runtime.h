@@ -82,7 +82,7 @@ struct psc_lattice {
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3, 0, 1000000, 0};
+    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3, 0, 1000000, 0, 0, 0};
     int64_t launches = 0;
     uint64_t events = 0;
     uint64_t h2d = 0, d2h = 0;
@@ -93,6 +93,23 @@ struct psc_lattice {
     std::vector<cudaEvent_t> event_pool;
     int sticky = PSC_OK;
     std::vector<void*> allocs;
+
+    // tile kernel buffers (allocated on first use, grown when a plan needs more)
+    struct TileBuffers {
+        int64_t slots = 0;             // regions x cap
+        int32_t regions = 0;
+        int64_t ids = 0;               // entries of img_id
+        int32_t* b_vox[2] = {nullptr, nullptr};
+        uint32_t* b_ids[2] = {nullptr, nullptr};
+        uint32_t* b_state = nullptr;
+        int32_t* b_cnt = nullptr;
+        int32_t* in_vox = nullptr;
+        uint32_t* in_ids = nullptr;
+        int32_t* in_cnt = nullptr;
+        uint32_t* done = nullptr;
+        uint64_t* img_id = nullptr;
+    } tile;
+    int tile_smem = -1;                // shared memory a tile block may use (-1: not queried yet)
 };
 
 namespace psc_rt {
@@ -114,5 +131,9 @@ int check_device(psc_lattice* L);
 int drive(psc_lattice* L, double t_end, int64_t max_events);
 // Morton re-sort of species s's list (queued on the lattice's stream)
 int resort(psc_lattice* L, int s);
+void dev_free_one(psc_lattice* L, void* p);
+// Can stretches of species s run under the tile kernel?  Fills the plan.
+bool tile_plan(psc_lattice* L, int s, TilePlan* P);
+int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P);
 
 }  // namespace psc_rt

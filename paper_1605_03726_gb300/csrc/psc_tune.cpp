@@ -22,7 +22,7 @@ using namespace psc_rt;
 namespace {
 
 struct Trial {
-    int32_t persistent, run_per_thread, block_threads, blocks_per_sm, resort_period;
+    int32_t persistent, run_per_thread, block_threads, blocks_per_sm, resort_period, tiles;
 };
 
 void apply(psc_lattice* L, const Trial& t)
@@ -32,12 +32,13 @@ void apply(psc_lattice* L, const Trial& t)
     L->opt.block_threads = t.block_threads;
     L->opt.blocks_per_sm = t.blocks_per_sm;
     L->opt.resort_period = t.resort_period;
+    L->opt.tiles = t.tiles;
 }
 
 Trial current(const psc_lattice* L)
 {
     return {L->opt.persistent, L->opt.run_per_thread, L->opt.block_threads, L->opt.blocks_per_sm,
-            L->opt.resort_period};
+            L->opt.resort_period, L->opt.tiles};
 }
 
 struct Timer {
@@ -152,15 +153,20 @@ extern "C" int psc_autotune(psc_lattice* L, int64_t max_events, psc_tune_result*
                 if (!rc && us < best_us) { best = t; best_us = us; }
             }
         }
-        // 2. persistent stretches and molecules per thread
+        // 2. persistent stretches: the tile kernel, or molecules per thread of
+        //    the molecule-list kernel, or none
         if (any_run) {
-            const Trial cand[] = {{1, 0, 0, 0, 0}, {1, 8, 0, 0, 0}, {1, 16, 0, 0, 0}, {-1, 0, 0, 0, 0}};
+            const Trial cand[] = {{1, 0, 0, 0, 0, 1}, {1, 0, 0, 0, 0, -1}, {1, 8, 0, 0, 0, -1}, {1, 16, 0, 0, 0, -1},
+                                  {-1, 0, 0, 0, 0, -1}};
             for (const Trial& c : cand) {
                 if (rc || T.budget <= 0) break;
                 Trial t = best;
                 t.persistent = c.persistent;
                 t.run_per_thread = c.run_per_thread;
-                if ((t.persistent > 0) == (best.persistent > 0) && t.run_per_thread == best.run_per_thread) continue;
+                t.tiles = c.tiles;
+                if ((t.persistent > 0) == (best.persistent > 0) && t.run_per_thread == best.run_per_thread &&
+                    t.tiles == best.tiles)
+                    continue;
                 double us;
                 rc = run_trial(t, W, false, &us);
                 if (!rc && us < best_us) { best = t; best_us = us; }
@@ -192,6 +198,7 @@ extern "C" int psc_autotune(psc_lattice* L, int64_t max_events, psc_tune_result*
     out->block_threads = best.block_threads;
     out->blocks_per_sm = best.blocks_per_sm;
     out->resort_period = best.resort_period;
+    out->tiles = best.tiles;
     out->trials = T.trials;
     out->events = T.ran;
     out->us_per_event = best_us;

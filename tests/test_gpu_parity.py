@@ -224,3 +224,48 @@ def test_diffusion_512cubed_full_size():
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, chunk)
+
+
+# Owner-computes tile kernel (forced on, with a given number of boxes): every
+# stretch scatters the list into boxes, runs, and gathers it back; molecules
+# cross boxes every event.  Shapes: periodic with whole bricks, reflective
+# ragged, one periodic axis; densities from sparse to crowded.
+TILE_CASES = [
+    ((48, 44, 40), psc.PERIODIC_ALL, 0.01, 1),
+    ((48, 44, 40), psc.PERIODIC_ALL, 0.05, 8),
+    ((48, 44, 40), psc.PERIODIC_ALL, 0.30, 0),
+    ((36, 30, 26), 0, 0.10, 0),
+    ((36, 30, 26), 0, 0.60, 5),
+    ((40, 30, 22), psc.PERIODIC_I, 0.20, 0),
+    ((8, 8, 4), psc.PERIODIC_ALL, 0.25, 0),
+]
+
+
+@pytest.mark.parametrize("claim_table", [1, 2])
+@pytest.mark.parametrize("shape,boundary,frac,regions", TILE_CASES)
+def test_tile_kernel_matches_oracle(shape, boundary, frac, regions, claim_table):
+    n = max(1, int(frac * shape[0] * shape[1] * shape[2]))
+    g, o = build_both(shape, lambda L: models.diffusion_only(L, n), 21, boundary=boundary,
+                      claim_table=claim_table, tiles=1, tile_regions=regions)
+    for chunk in (1, 7, 40):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+
+
+def _walkers_and_crowders(L, V):
+    # immobile crowders, two walker species with different hop intervals
+    L.add_species(0.0, int(0.2 * V))
+    L.add_species(2e-12, int(0.03 * V))
+    L.add_species(5e-12, int(0.02 * V))
+
+
+@pytest.mark.parametrize("claim_table", [1, 2])
+def test_tile_kernel_interleaved_species_with_crowders(claim_table):
+    shape = (44, 40, 36)
+    V = shape[0] * shape[1] * shape[2]
+    g, o = build_both(shape, lambda L: _walkers_and_crowders(L, V), 4, claim_table=claim_table, tiles=1)
+    for chunk in (5, 60):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)

@@ -185,11 +185,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes of one k_hop_run launch from the committed ncu summary
-    (profiles/hop_run_512cubed_traffic.txt), with the kernel revision it was
+def profiled_traffic(name):
+    """DRAM bytes of one launch of the timed stretch kernel from the committed
+    ncu summary (profiles/<name>_traffic.txt), with the kernel revision it was
     taken on; None if absent."""
-    p = os.path.join(ROOT, "profiles", "hop_run_512cubed_traffic.txt")
+    p = os.path.join(ROOT, "profiles", name + "_traffic.txt")
     try:
         d = {}
         with open(p) as f:
@@ -269,7 +269,8 @@ def gpu_arm(args, rank, world, local):
     hop_ms = kt["claim_ms"] + kt["commit_ms"] + kt["run_ms"]
     t_event_ms = hop_ms / n_ev
     achieved = b_alg * N_MOL / (t_event_ms * 1e-3) / 1e9
-    tr = profiled_traffic()
+    tiles_used = kt.get("tile_launches", 0) > 0
+    tr = profiled_traffic("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
     traffic = None
     events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
     if persistent and tr and tr.get("kernel_rev") == kernel_revision() and \
@@ -278,10 +279,13 @@ def gpu_arm(args, rank, world, local):
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
         "frac": round(achieved / hbm, 4), "traffic": traffic,
-        "traffic_unit": "DRAM bytes per launch (ncu, profiles/hop_run_512cubed.md)",
+        "traffic_unit": "DRAM bytes per launch (ncu, profiles/%s.md)" % ("tile_run_512cubed" if tiles_used
+                                                                          else "hop_run_512cubed"),
         "events_per_launch": events_per_launch,
         "bytes_alg_per_launch": round(b_alg * N_MOL * events_per_launch),
-        "kernel": ("k_hop_run (persistent: claim phase, grid barrier, commit phase per event)" if persistent
+        "kernel": ("k_tile_run (owner-computes boxes in shared memory, neighbour waits; one launch per stretch, "
+                   "with k_tile_scatter / k_tile_gather)" if tiles_used
+                   else "k_hop_run (persistent: claim phase, grid barrier, commit phase per event)" if persistent
                    else "k_claim + k_commit (one hop event over all molecules)"),
         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
         "bytes_alg_per_attempt": round(b_alg, 3), "hop_success": round(s_frac, 5),
@@ -304,7 +308,7 @@ def kernel_revision():
     """Hash of the kernel sources: ncu traffic is reported only for the kernels it was taken on."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("psc_kernels.cu", "psc_internal.h"):
+    for name in ("psc_kernels.cu", "psc_tiles.cuh", "psc_internal.h"):
         with open(os.path.join(ROOT, "paper_1605_03726_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -108,6 +108,7 @@ typedef struct {
     int64_t claim_launches, commit_launches, reconcile_events, resorts;
     double run_ms;            /* persistent launches over stretches of events  */
     int64_t run_launches, run_events;
+    int64_t tile_launches, tile_events;   /* of those, under the tile kernel   */
 } psc_kernel_times;
 
 /* Tunables; zero in a field keeps the current value. */
@@ -280,7 +281,8 @@ double psc_tau(const psc_lattice *L, int32_t species);
 double psc_p_ab(const psc_lattice *L, int32_t reaction);
 
 /* Bytes of device memory the lattice holds after psc_populate (or would hold,
-   computed from its shape and model, before). */
+   computed from its shape and model, before), including the tile kernel's
+   buffers once a stretch has run under it. */
 int psc_device_bytes(const psc_lattice *L, int64_t *bytes);
 
 /* Free the lattice and its device memory (waits for its queued work). */

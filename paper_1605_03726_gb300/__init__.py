@@ -43,7 +43,8 @@ class KernelTimes(ctypes.Structure):
                 ("reconcile_ms", ctypes.c_double), ("resort_ms", ctypes.c_double),
                 ("claim_launches", ctypes.c_int64), ("commit_launches", ctypes.c_int64),
                 ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64),
-                ("run_ms", ctypes.c_double), ("run_launches", ctypes.c_int64), ("run_events", ctypes.c_int64)]
+                ("run_ms", ctypes.c_double), ("run_launches", ctypes.c_int64), ("run_events", ctypes.c_int64),
+                ("tile_launches", ctypes.c_int64), ("tile_events", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))

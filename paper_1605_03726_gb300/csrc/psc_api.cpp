@@ -127,7 +127,7 @@ EventArgs event_args(const psc_lattice* L, int s)
     return a;
 }
 
-enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort, kSpanRun };
+enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort, kSpanRun, kSpanTile };
 
 cudaEvent_t take_event(psc_lattice* L)
 {
@@ -279,10 +279,9 @@ bool tile_plan(psc_lattice* L, int s, TilePlan* P)
     if ((L->bflags & PSC_PERIODIC_I) && (L->ni & 3)) return false;
     if ((L->bflags & PSC_PERIODIC_J) && (L->nj & 3)) return false;
     if ((L->bflags & PSC_PERIODIC_K) && (L->nk & 1)) return false;
-    if (L->tables[0] && L->hash_bits[s] > 26) return false;
     if (L->tile_smem < 0) L->tile_smem = tile_smem_limit(L->device);
     const int nbi = (L->ni + 3) / 4, nbj = (L->nj + 3) / 4, nbk = (L->nk + 1) / 2;
-    int S = L->sm_count;
+    int S = kTileBlocksPerSM * L->sm_count;
     if (L->opt.tile_regions > 0) S = std::min(S, L->opt.tile_regions);
     // the cut that minimises the largest box (work of the slowest block), then
     // the halo
@@ -322,7 +321,7 @@ static int tile_buffers(psc_lattice* L, const TilePlan& P, int64_t ids)
     if (slots > T.slots || P.regions > T.regions) {
         for (void* p : {(void*)T.b_vox[0], (void*)T.b_vox[1], (void*)T.b_ids[0], (void*)T.b_ids[1],
                         (void*)T.b_state, (void*)T.b_cnt, (void*)T.in_vox, (void*)T.in_ids, (void*)T.in_cnt,
-                        (void*)T.done})
+                        (void*)T.claimed, (void*)T.done})
             if (p) dev_free_one(L, p);
         const int64_t ns = std::max(slots, T.slots);
         const int32_t nr = std::max(P.regions, T.regions);
@@ -335,14 +334,21 @@ static int tile_buffers(psc_lattice* L, const TilePlan& P, int64_t ids)
         T.in_ids = (uint32_t*)dev_alloc(L, (size_t)ns * 4);
         T.b_cnt = (int32_t*)dev_alloc(L, (size_t)nr * 4);
         T.in_cnt = (int32_t*)dev_alloc(L, (size_t)nr * 4);
+        T.claimed = (uint32_t*)dev_alloc(L, (size_t)nr * 4);
         T.done = (uint32_t*)dev_alloc(L, (size_t)nr * 4);
         T.slots = ns;
         T.regions = nr;
         if (!T.b_vox[0] || !T.b_vox[1] || !T.b_ids[0] || !T.b_ids[1] || !T.b_state || !T.in_vox || !T.in_ids ||
-            !T.b_cnt || !T.in_cnt || !T.done) {
+            !T.b_cnt || !T.in_cnt || !T.claimed || !T.done) {
             T.slots = 0;
             return PSC_E_NOMEM;
         }
+    }
+    if (!L->claim && !T.claim) {
+        // contested targets are claimed in per-voxel words, free (all ones) between events
+        T.claim = (uint32_t*)dev_alloc(L, (size_t)L->V * 4);
+        if (!T.claim) return PSC_E_NOMEM;
+        launch_fill_u32(T.claim, kNoClaim, (size_t)L->V, L->sm_count * 8, L->stream);
     }
     if (ids > T.ids) {
         if (T.img_id) dev_free_one(L, T.img_id);
@@ -360,25 +366,19 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     for (int q = 0; q < s; ++q) id_lo += L->sp[q].n0;
     int rc = tile_buffers(L, P, L->sp[s].n0);
     if (rc) return rc;
-    // the one claim table must start empty
-    for (int t = 0; t < 2; ++t) {
-        if (L->tables[t] && L->table_used[t]) {
-            launch_fill_u64(L->tables[t], kEmptySlot, L->table_used[t], L->sm_count * 4, st);
-            L->table_used[t] = 0;
-            L->launches += 1;
-        }
-    }
     TileArgs A{};
     A.ev = event_args(L, s);
     A.ev.ct.hash = nullptr;
     A.ev.ct.clear = nullptr;
     A.ev.ct.clear_n = 0;
-    A.tables[0] = L->tables[0];
-    A.tables[1] = L->tables[1];
+    A.claim = L->claim ? L->claim : L->tile.claim;
+    A.claimed = L->tile.claimed;
     A.done = L->tile.done;
-    // neighbour waits between events need boxes at least two bricks thick
-    // (then everything an event reads from outside its box was written by
-    // adjacent boxes)
+    // Neighbour waits instead of grid barriers need boxes at least two bricks
+    // thick: then everything a phase reads from outside its box (halo bits,
+    // arrivals, the claim words of targets next to it) is written only by
+    // boxes adjacent to it, and all boxes touching one claim word are
+    // adjacent to each other.
     A.nbr_sync = (P.nbi / P.pi >= 2 && P.nbj / P.pj >= 2 && P.nbk / P.pk >= 2) ? 1 : 0;
     A.plan = P;
     for (int x = 0; x < 2; ++x) {
@@ -399,6 +399,7 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.b_cnt, 0, (size_t)P.regions * 4, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.in_cnt, 0, (size_t)P.regions * 4, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.done, 0, (size_t)P.regions * 4, st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->tile.claimed, 0, (size_t)P.regions * 4, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st)))) return rc;
     cudaEvent_t sp = span_open(L);
     const int64_t n = L->sp[s].n0;
@@ -406,7 +407,7 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     launch_tile_scatter(A, sblocks, st);
     rc = cuda_fail(L, launch_tile_run(A, st));
     if (!rc) launch_tile_gather(A, st);
-    span_close(L, sp, kSpanRun, n_events);
+    span_close(L, sp, kSpanTile, n_events);
     if (rc) return rc;
     L->launches += 3;
     L->events += (uint64_t)n_events;
@@ -1082,6 +1083,10 @@ int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
         case kSpanCommit: out->commit_ms += ms; out->commit_launches++; break;
         case kSpanReconcile: out->reconcile_ms += ms; out->reconcile_events++; break;
         case kSpanRun: out->run_ms += ms; out->run_launches++; out->run_events += sp.events; break;
+        case kSpanTile:
+            out->run_ms += ms; out->run_launches++; out->run_events += sp.events;
+            out->tile_launches++; out->tile_events += sp.events;
+            break;
         default: out->resort_ms += ms; out->resorts++; break;
         }
         L->event_pool.push_back(sp.a);
@@ -1112,6 +1117,10 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
     } else {
         b += 2 * N * 16 + 2 * N * 8;
     }
+    // tile kernel buffers, once a stretch has used them
+    const auto& T = L->tile;
+    b += T.slots * 4 * 5 + (int64_t)T.regions * 4 * 4 + T.ids * 8;
+    if (T.claim) b += L->V * 4;
     *bytes = b;
     return PSC_OK;
 }

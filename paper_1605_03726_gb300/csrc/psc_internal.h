@@ -176,9 +176,10 @@ struct TilePlan {
 struct TileArgs {
     EventArgs ev;              // g = index of the first event
     TilePlan plan;
-    uint64_t* tables[2];       // claim tables (hash mode), by event parity; null: per-voxel words
+    uint32_t* claim;           // per-voxel claim words (kNoClaim when free), for contested targets
+    uint32_t* claimed;         // [regions] events whose claim phase the region has finished
     uint32_t* done;            // [regions] events whose commit phase the region has finished
-    int32_t nbr_sync;          // 1: between events wait for the neighbouring boxes only
+    int32_t nbr_sync;          // 1: phases wait for the neighbouring boxes only; 0: grid barriers
     int32_t* b_vox[2];         // [regions][cap] voxel of each molecule; event e
     uint32_t* b_ids[2];        // reads buffer e & 1 and keeps its survivors in the other
     uint32_t* b_state;         // claim-phase decision of each bucket slot
@@ -218,14 +219,15 @@ cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread
 // the three launches of a stretch (list -> buckets, the persistent events,
 // buckets -> list)
 int tile_smem_limit(int device);
-constexpr int kTileOutbox = 2048;           // departures a block stages per event
-constexpr int kTileQueue = 2048;            // molecules a block defers per phase (contested, leaving)
+constexpr int kTileOutbox = 1024;           // departures a block stages per event
+constexpr int kTileQueue = 1024;            // molecules a block defers per commit phase (contested, leaving)
 inline int tile_smem_bytes(const TilePlan& P)
 {
     return ((P.box_words + 3) & ~3) * 4 + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
            ((P.nbi + P.nbj + P.nbk + 15) & ~15);
 }
-constexpr int kTileThreads = 1024;
+constexpr int kTileThreads = 512;
+constexpr int kTileBlocksPerSM = 2;
 void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st);
 void launch_tile_gather(const TileArgs& A, cudaStream_t st);

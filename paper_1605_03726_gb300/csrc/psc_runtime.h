@@ -106,8 +106,10 @@ struct psc_lattice {
         int32_t* in_vox = nullptr;
         uint32_t* in_ids = nullptr;
         int32_t* in_cnt = nullptr;
+        uint32_t* claimed = nullptr;
         uint32_t* done = nullptr;
         uint64_t* img_id = nullptr;
+        uint32_t* claim = nullptr;     // per-voxel claim words when the lattice has none
     } tile;
     int tile_smem = -1;                // shared memory a tile block may use (-1: not queried yet)
 };

@@ -297,12 +297,15 @@ __device__ __forceinline__ void tile_ingest(const TileArgs& A, int r, const Tile
 }
 
 // Wait until every box next to region r (up to 26, across periodic wraps)
-// has finished the commit phase of event target - 1 (done[q] >= target).
-// Bounded like the grid barrier; false (error raised) on time-out.
-__device__ __forceinline__ bool tile_wait_neighbours(const TileArgs& A, int r, uint32_t target, int* s_flag)
+// has published flags[q] >= target.  Bounded like the grid barrier; false
+// (error raised) on time-out.  A nonzero barrier_phantom (tests of the
+// time-out path) raises the target beyond anything published.
+__device__ __forceinline__ bool tile_wait_neighbours(const TileArgs& A, const uint32_t* flags, int r,
+                                                     uint32_t target, int* s_flag)
 {
     const TilePlan& P = A.plan;
     const uint32_t bf = A.ev.geo.bflags;
+    target += A.barrier_phantom ? 0x40000000u : 0u;
     if (threadIdx.x == 0) *s_flag = 1;
     __syncthreads();
     if (threadIdx.x < 27 && threadIdx.x != 13) {
@@ -314,7 +317,7 @@ __device__ __forceinline__ bool tile_wait_neighbours(const TileArgs& A, int r, u
         if (rj < 0 || rj >= P.pj) { if (bf & 2u) rj = (rj + P.pj) % P.pj; else skip = true; }
         if (rk < 0 || rk >= P.pk) { if (bf & 4u) rk = (rk + P.pk) % P.pk; else skip = true; }
         if (!skip) {
-            const volatile uint32_t* f = A.done + (rk * P.pj + rj) * P.pi + ri;
+            const volatile uint32_t* f = flags + (rk * P.pj + rj) * P.pi + ri;
             uint64_t t0 = 0;
             for (unsigned int spins = 0; *f < target; ++spins) {
                 if ((spins & 1023u) == 0u) {
@@ -471,11 +474,20 @@ __device__ __forceinline__ void tile_target_global(const Geometry& G, const Tile
     nb.t = nb.i + G.ni * (nb.j + G.nj * nb.k);
 }
 
-template <bool HASH>
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
+// Publish that region r has finished a phase of the event (flags[r] = value)
+__device__ __forceinline__ void tile_publish(uint32_t* flags, int r, uint32_t value)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&flags[r], value);
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(const TileArgs A)
 {
     extern __shared__ uint32_t smem[];
-    // s_misc: arrivals, survivors, outbox entries, wait flag, claim queue, commit queue
+    // s_misc: arrivals, survivors, outbox entries, wait flag, -, commit queue
     __shared__ int s_misc[6];
     const EventArgs& a = A.ev;
     const Geometry& G = a.geo;
@@ -488,7 +500,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
     const int cap = A.plan.cap;
     const int64_t base = (int64_t)r * cap;
     const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
-    constexpr int U = 4;                                 // molecules whose memory operations go out together
+    uint32_t* claim = A.claim;
+    constexpr int U = 2;                                 // molecules whose memory operations go out together
     // box coordinates of the lattice along reflective axes (targets outside are walls)
     const int xlo = (G.bflags & 1u) ? INT_MIN : 4 - 4 * b.bi0, xhi = (G.bflags & 1u) ? INT_MAX : xlo + G.ni;
     const int ylo = (G.bflags & 2u) ? INT_MIN : 4 - 4 * b.bj0, yhi = (G.bflags & 2u) ? INT_MAX : ylo + G.nj;
@@ -510,7 +523,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
         decode(G, (uint32_t)A.b_vox[0][base + x], i, j, k);
         A.b_vox[0][base + x] = (int32_t)tile_pack(i - 4 * b.bi0, j - 4 * b.bj0, k - 2 * b.bk0);
     }
-    if (threadIdx.x == 0) s_misc[5] = 0;
     unsigned long long n_att = 0, n_hop = 0;
     __syncthreads();
     for (int e = 0; e < A.n_events; ++e) {
@@ -519,15 +531,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
         const int32_t* bv = A.b_vox[cur] + base;
         const uint32_t* bi = A.b_ids[cur] + base;
         uint32_t* bs = A.b_state + base;
-        uint64_t* tab = A.tables[cur];                   // claim tables alternate with the event
         if (e > 0) {
-            if (A.nbr_sync && !tile_wait_neighbours(A, r, (uint32_t)e, &s_misc[3])) return;
+            // the neighbours' last commits: halo bits, arrivals, reset claim words
+            if (A.nbr_sync && !tile_wait_neighbours(A, A.done, r, (uint32_t)e, &s_misc[3])) return;
             tile_ingest(A, r, b, box, n, cur, s_misc);
             tile_refresh_halo(G, A.plan, b, div_bi, div_bj2, a.bits, box);
+            __syncthreads();
         }
-        if (threadIdx.x == 0) s_misc[4] = 0;
-        __syncthreads();
-        // ---- claim phase: draws, targets, unclaimed hops; contested targets queued ----
+        // ---- claim phase ----
         for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
             uint32_t vv[U], ii[U];
 #pragma unroll
@@ -553,83 +564,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
                         st |= kTileMove;                 // only the mover itself is next to the target
                     } else if (!(box[((tz >> 1) * b.BJ + (ty >> 2)) * b.BI + (tx >> 2)] &
                                  (1u << ((tx & 3) | ((ty & 3) << 2) | ((tz & 1) << 4))))) {
-                        // vacant, but other molecules can reach it: claim it after the loop
-                        const int k = atomicAdd(&s_misc[4], 1);
-                        if (k < kTileQueue) {
-                            S.queue[k] = xm;
-                        } else {
-                            Nb nb;
-                            tile_target_global(G, b, vv[u], d, nb);
-                            if (HASH) {
-                                const int32_t slot = hash_claim_from(
-                                    tab, a.ct.hash_bits, (uint32_t)nb.t, ii[u],
-                                    slot_of(G, (uint32_t)nb.t, nb.i, nb.j, nb.k, a.ct.hash_bits),
-                                    __ldcg((const unsigned long long*)&tab[slot_of(G, (uint32_t)nb.t, nb.i, nb.j,
-                                                                                   nb.k, a.ct.hash_bits)]),
-                                    &a.sc->err);
-                                if (slot >= 0) st |= kTileClaimed | (uint32_t)slot;
-                            } else {
-                                atomicMin(&a.ct.direct[nb.t], ii[u]);
-                                st |= kTileClaimed;
-                            }
-                        }
+                        // vacant, but other molecules can reach it: the lowest id wins
+                        int32_t i, j, k;
+                        uint64_t w;
+                        tile_global(G, b, tx, ty, tz, i, j, k, w);
+                        atomicMin(&claim[i + G.ni * (j + G.nj * k)], ii[u]);
+                        st |= kTileClaimed;
                     }
                 }
                 bs[xm] = st;
-            }
-        }
-        __syncthreads();
-        {
-            // queued claims, all lanes busy, a batch's atomics in flight together
-            const int m = min(s_misc[4], kTileQueue);
-            for (int c0 = 0; c0 < m; c0 += U * blockDim.x) {
-                int32_t xx[U], tt[U];
-                uint32_t ii[U], ss[U], hh[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = c0 + u * blockDim.x + threadIdx.x;
-                    xx[u] = k < m ? S.queue[k] : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    tt[u] = -1;
-                    hh[u] = 0u;
-                    ii[u] = 0u;
-                    ss[u] = 0u;
-                    if (xx[u] < 0) continue;
-                    const uint32_t w = (uint32_t)__ldcg(bv + xx[u]);
-                    ii[u] = __ldcg(bi + xx[u]);
-                    ss[u] = __ldcg(bs + xx[u]);
-                    Nb nb;
-                    tile_target_global(G, b, w, (int)((ss[u] >> 26) & 15u), nb);
-                    tt[u] = nb.t;
-                    if (HASH) hh[u] = slot_of(G, (uint32_t)nb.t, nb.i, nb.j, nb.k, a.ct.hash_bits);
-                }
-                if (HASH) {
-                    unsigned long long prev[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        prev[u] = tt[u] >= 0 ? atomicCAS((unsigned long long*)&tab[hh[u]],
-                                                         (unsigned long long)kEmptySlot,
-                                                         (unsigned long long)(((uint64_t)tt[u] << 32) | ii[u]))
-                                             : 0ull;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (tt[u] < 0) continue;
-                        const int32_t slot = prev[u] == kEmptySlot
-                                                 ? (int32_t)hh[u]
-                                                 : hash_claim_from(tab, a.ct.hash_bits, (uint32_t)tt[u], ii[u], hh[u],
-                                                                   prev[u], &a.sc->err);
-                        if (slot >= 0) bs[xx[u]] = ss[u] | kTileClaimed | (uint32_t)slot;
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        if (tt[u] < 0) continue;
-                        atomicMin(&a.ct.direct[tt[u]], ii[u]);
-                        bs[xx[u]] = ss[u] | kTileClaimed;
-                    }
-                }
             }
         }
         n_att += (unsigned long long)n;
@@ -638,7 +581,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
             s_misc[2] = 0;
             s_misc[5] = 0;
         }
-        if (!grid_barrier(A.barrier, &a.sc->err, A.barrier_timeout_ns, A.barrier_phantom)) return;
+        if (A.nbr_sync) {
+            // a claim word is touched only by boxes that are all neighbours of each other
+            tile_publish(A.claimed, r, (uint32_t)(e + 1));
+            if (!tile_wait_neighbours(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;
+        } else if (!grid_barrier(A.barrier, &a.sc->err, A.barrier_timeout_ns, A.barrier_phantom)) {
+            return;
+        }
         // ---- commit phase: hops inside the box here, everything else queued ----
         int32_t* ov = A.b_vox[cur ^ 1] + base;
         uint32_t* oi = A.b_ids[cur ^ 1] + base;
@@ -681,16 +630,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
                         // queue full: handle it here
                         bool win = (st & kTileMove) != 0u;
                         if (!win) {
-                            if (HASH) {
-                                uint64_t* slotp = &tab[st & kTileSlotMask];
-                                win = (uint32_t)__ldcg((const unsigned long long*)slotp) == ii[u];
-                                if (win) *slotp = kEmptySlot;
-                            } else {
-                                Nb nb;
-                                tile_target_global(G, b, w, (int)((st >> 26) & 15u), nb);
-                                win = __ldcg(&a.ct.direct[nb.t]) == ii[u];
-                                if (win) a.ct.direct[nb.t] = kNoClaim;
-                            }
+                            Nb nb;
+                            tile_target_global(G, b, w, (int)((st >> 26) & 15u), nb);
+                            win = __ldcg(&claim[nb.t]) == ii[u];
+                            if (win) claim[nb.t] = kNoClaim;
                         }
                         if (win) {
                             uint32_t neww = w;
@@ -723,14 +666,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
                     rb[u] = 0u;
                     tt[u] = -1;
                     if (!(ss[u] & kTileClaimed)) continue;
-                    if (HASH) {
-                        rb[u] = (uint32_t)__ldcg((const unsigned long long*)&tab[ss[u] & kTileSlotMask]);
-                    } else {
-                        Nb nb;
-                        tile_target_global(G, b, vv[u], (int)((ss[u] >> 26) & 15u), nb);
-                        tt[u] = nb.t;
-                        rb[u] = __ldcg(&a.ct.direct[nb.t]);
-                    }
+                    Nb nb;
+                    tile_target_global(G, b, vv[u], (int)((ss[u] >> 26) & 15u), nb);
+                    tt[u] = nb.t;
+                    rb[u] = __ldcg(&claim[nb.t]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -740,8 +679,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
                     bool win = (st & kTileMove) != 0u;
                     if ((st & kTileClaimed) && rb[u] == ii[u]) {
                         win = true;
-                        if (HASH) tab[st & kTileSlotMask] = kEmptySlot;
-                        else a.ct.direct[tt[u]] = kNoClaim;
+                        claim[tt[u]] = kNoClaim;         // the winner resets the word
                     }
                     if (keep && win) {
                         uint32_t neww = w;
@@ -770,18 +708,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_run(const TileArgs A)
             }
         }
         if (A.nbr_sync) {
-            // the next event needs only the neighbours' commits (halo, inbox)
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicExch(&A.done[r], (uint32_t)(e + 1));
-            }
+            tile_publish(A.done, r, (uint32_t)(e + 1));
         } else if (!grid_barrier(A.barrier, &a.sc->err, A.barrier_timeout_ns, A.barrier_phantom)) {
             return;
         }
     }
     // the last event's arrivals, then the region's bits back to the mirror
-    if (A.n_events > 0 && A.nbr_sync && !tile_wait_neighbours(A, r, (uint32_t)A.n_events, &s_misc[3])) return;
+    if (A.n_events > 0 && A.nbr_sync && !tile_wait_neighbours(A, A.done, r, (uint32_t)A.n_events, &s_misc[3]))
+        return;
     if (A.n_events > 0) tile_ingest(A, r, b, box, n, A.n_events & 1, s_misc);
     __syncthreads();
     for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
@@ -881,9 +815,13 @@ __global__ void __launch_bounds__(256) k_tile_gather(const TileArgs A)
 
 int tile_smem_limit(int device)
 {
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
-    return optin - 1024;                                 // static shared memory and slack
+    int optin = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess)
+        return 0;
+    // kTileBlocksPerSM blocks share an SM; each also reserves 1 KB, plus static shared memory and slack
+    const int share = per_sm / kTileBlocksPerSM - 2048;
+    return optin - 1024 < share ? optin - 1024 : share;
 }
 
 void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st)
@@ -897,25 +835,19 @@ void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st)
     k_tile_scatter<<<blocks, 1024, smem, st>>>(A);
 }
 
-template <bool HASH>
-static cudaError_t launch_tile_run_t(const TileArgs& A, cudaStream_t st)
+cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st)
 {
     const size_t smem = (size_t)tile_smem_bytes(A.plan);
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_tile_run<HASH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_tile_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     void* args[] = {const_cast<TileArgs*>(&A)};
-    return cudaLaunchCooperativeKernel((const void*)k_tile_run<HASH>, dim3(A.plan.regions), dim3(kTileThreads),
-                                       args, smem, st);
-}
-
-cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st)
-{
-    return A.tables[0] ? launch_tile_run_t<true>(A, st) : launch_tile_run_t<false>(A, st);
+    return cudaLaunchCooperativeKernel((const void*)k_tile_run, dim3(A.plan.regions), dim3(kTileThreads), args,
+                                       smem, st);
 }
 
 void launch_tile_gather(const TileArgs& A, cudaStream_t st)

@@ -65,6 +65,31 @@ def test_barrier_wait_runs_out_and_is_reported():
     G.close()
 
 
+def test_tile_neighbour_wait_runs_out_and_is_reported():
+    # the tile kernel's phases wait on neighbouring boxes' flags, bounded the same way
+    L = psc.Lattice(*SHAPE, voxel_radius=1e-8)
+    L.set_options(persistent=1, tiles=1, tile_regions=8, barrier_timeout_us=20000, barrier_phantom=1)
+    _walkers(L)
+    t0 = time.monotonic()
+    L.run_events(4)
+    with pytest.raises(psc.EngineError) as err:
+        L.synchronize()
+    assert err.value.rc == psc.E_TIMEOUT
+    assert time.monotonic() - t0 < 10.0
+    L.close()
+    G = psc.Lattice(*SHAPE, voxel_radius=1e-8)
+    G.set_options(persistent=1, tiles=1, tile_regions=8)
+    s = _walkers(G)
+    G.run_events(8)
+    o = oracle.Lattice(*SHAPE, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
+    o.add_species(D, N)
+    o.populate(17)
+    o.run_events(8)
+    a, b = G.coords(s), o.coords(s)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    G.close()
+
+
 class _FailingAllocator:
     """Device memory from PyTorch's caching allocator; the allocation numbered
     `fail_at` (0-based) returns NULL."""

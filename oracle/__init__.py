@@ -15,6 +15,7 @@ W_PCLAMP = 1
 RULE_SYNC, RULE_SEQ_ID, RULE_SEQ_RANDOM = 0, 1, 2
 PERIODIC_I, PERIODIC_J, PERIODIC_K = 1, 2, 4
 PERIODIC_ALL = 7
+FCC = 8                  # lattice flag: FCC (ABC stacking) instead of HCP
 
 _lib = None
 
@@ -59,6 +60,7 @@ def lib():
             "psco_philox4x32_10": (None, [P, P, P]),
             "psco_neighbor": (ctypes.c_int, [P, i32, i32, i32, i32, P, P]),
             "psco_center": (None, [i32, i32, i32, P]),
+            "psco_center_fcc": (None, [i32, i32, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -83,6 +85,12 @@ def philox(ctr, key):
 
 def threshold(p):
     return int(lib().psco_threshold(float(p)))
+
+
+def center_fcc(i, j, k):
+    o = np.zeros(3)
+    lib().psco_center_fcc(i, j, k, _ptr(o))
+    return o
 
 
 def center(i, j, k):

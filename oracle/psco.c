@@ -132,6 +132,47 @@ void psco_center(int32_t i, int32_t j, int32_t k, double xyz[3])
     xyz[2] = 2.0 * sqrt(2.0 / 3.0) * k;
 }
 
+/* FCC (App. B, figures only; derived here): the same triangular layers in
+   ABC stacking.  Layer k sits at (0, 0), (1, 1/sqrt(3)) or (0, 2/sqrt(3))
+   for k mod 3 = 0, 1, 2, so with c = k mod 3 and row parity
+   p = (j + [c == 1]) & 1 the centre is x = 2i + p, y = sqrt(3) j + c/sqrt(3),
+   z = 2 sqrt(2/3) k; layers k and k+3 coincide. */
+void psco_center_fcc(int32_t i, int32_t j, int32_t k, double xyz[3])
+{
+    int c = ((k % 3) + 3) % 3;
+    int p = (j + (c == 1)) & 1;
+    xyz[0] = 2.0 * i + p;
+    xyz[1] = sqrt(3.0) * j + (double)c / sqrt(3.0);
+    xyz[2] = 2.0 * sqrt(2.0 / 3.0) * k;
+}
+
+/* FCC neighbour offsets, d = 0..11 in the HCP order: the six in the layer as
+   for HCP; below, two at (i-1+p, i+p) on row j + a and one at (i, j + b) with
+   (a, b) = (-1, 0) for c = 0 and (0, +1) otherwise; above, two on row j + a'
+   and one at (i, j + b') with (a', b') = (+1, 0) for c = 2 and (0, -1)
+   otherwise. */
+static void raw_neighbor_fcc(int32_t i, int32_t j, int32_t k, int32_t d, int32_t o[3])
+{
+    int c = ((k % 3) + 3) % 3;
+    int p = (j + (c == 1)) & 1;
+    int ab = c == 0 ? -1 : 0, bb = c == 0 ? 0 : 1;
+    int aa = c == 2 ? 1 : 0, ba = c == 2 ? 0 : -1;
+    switch (d) {
+    case 0:  o[0] = i + 1;     o[1] = j;      o[2] = k;     break;
+    case 1:  o[0] = i - 1;     o[1] = j;      o[2] = k;     break;
+    case 2:  o[0] = i - 1 + p; o[1] = j - 1;  o[2] = k;     break;
+    case 3:  o[0] = i + p;     o[1] = j - 1;  o[2] = k;     break;
+    case 4:  o[0] = i - 1 + p; o[1] = j + 1;  o[2] = k;     break;
+    case 5:  o[0] = i + p;     o[1] = j + 1;  o[2] = k;     break;
+    case 6:  o[0] = i - 1 + p; o[1] = j + ab; o[2] = k - 1; break;
+    case 7:  o[0] = i + p;     o[1] = j + ab; o[2] = k - 1; break;
+    case 8:  o[0] = i;         o[1] = j + bb; o[2] = k - 1; break;
+    case 9:  o[0] = i - 1 + p; o[1] = j + aa; o[2] = k + 1; break;
+    case 10: o[0] = i + p;     o[1] = j + aa; o[2] = k + 1; break;
+    default: o[0] = i;         o[1] = j + ba; o[2] = k + 1; break;
+    }
+}
+
 /* the 12 neighbour offsets; d = 0..11 in this fixed order */
 static void raw_neighbor(int32_t i, int32_t j, int32_t k, int32_t d, int32_t o[3])
 {
@@ -158,7 +199,8 @@ int psco_neighbor(const psco_lattice *L, int32_t i, int32_t j, int32_t k, int32_
 {
     int32_t o[3];
     int32_t n[3] = { L->ni, L->nj, L->nk };
-    raw_neighbor(i, j, k, d, o);
+    if (L->bflags & PSCO_FCC) raw_neighbor_fcc(i, j, k, d, o);
+    else raw_neighbor(i, j, k, d, o);
     for (int a = 0; a < 3; ++a) {
         wrap[a] = 0;
         if (o[a] < 0 || o[a] >= n[a]) {
@@ -227,7 +269,7 @@ int psco_lattice_create(psco_lattice **out, int32_t ni, int32_t nj, int32_t nk,
 {
     if (!out) return PSCO_E_ARG;
     *out = NULL;
-    if (!(rv > 0.0) || !isfinite(rv) || bflags > 7u) return PSCO_E_ARG;
+    if (!(rv > 0.0) || !isfinite(rv) || bflags > 15u) return PSCO_E_ARG;
     if (rule < PSCO_RULE_SYNC || rule > PSCO_RULE_SEQ_RANDOM) return PSCO_E_ARG;
     if (ni < 1 || nj < 1 || nk < 1) return PSCO_E_DIMS;
     int64_t V = (int64_t)ni * nj * nk;
@@ -236,7 +278,8 @@ int psco_lattice_create(psco_lattice **out, int32_t ni, int32_t nj, int32_t nk,
        extents (Sec. 2.1), and 12 distinct neighbours need at least 3 / 4 / 4 */
     if ((bflags & PSCO_PERIODIC_I) && ni < 3) return PSCO_E_DIMS;
     if ((bflags & PSCO_PERIODIC_J) && (nj < 4 || (nj & 1))) return PSCO_E_DIMS;
-    if ((bflags & PSCO_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSCO_E_DIMS;
+    if (!(bflags & PSCO_FCC) && (bflags & PSCO_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSCO_E_DIMS;
+    if ((bflags & PSCO_FCC) && (bflags & PSCO_PERIODIC_K) && (nk < 3 || nk % 3)) return PSCO_E_DIMS;
     psco_lattice *L = (psco_lattice *)calloc(1, sizeof(psco_lattice));
     if (!L) return PSCO_E_NOMEM;
     L->ni = ni; L->nj = nj; L->nk = nk; L->V = V;
@@ -831,7 +874,8 @@ int psco_coords(const psco_lattice *L, int32_t s, int32_t *ijk, uint32_t *ids,
 
 /* unwrapped integer basis: X = 2I + P, Y = 3J + (K & 1), Z = K with
    I = i + img_i N_i (likewise J, K) and P = (J + K) & 1; the centre is then
-   (X, Y / sqrt(3), Z * 2 sqrt(2/3)) in units of r_v. */
+   (X, Y / sqrt(3), Z * 2 sqrt(2/3)) in units of r_v.  FCC: Y = 3J + (K mod 3)
+   and P = (J + [K mod 3 == 1]) & 1. */
 int psco_unwrapped(const psco_lattice *L, int32_t s, int32_t *xyz, uint32_t *ids,
                    int64_t cap, int64_t *n_out)
 {
@@ -849,8 +893,14 @@ int psco_unwrapped(const psco_lattice *L, int32_t s, int32_t *xyz, uint32_t *ids
         int32_t I = c[0] + (int32_t)M->img[0] * L->ni;
         int32_t J = c[1] + (int32_t)M->img[1] * L->nj;
         int32_t K = c[2] + (int32_t)M->img[2] * L->nk;
-        xyz[3 * a + 0] = 2 * I + ((J + K) & 1);
-        xyz[3 * a + 1] = 3 * J + (K & 1);
+        if (L->bflags & PSCO_FCC) {
+            int32_t c3 = ((K % 3) + 3) % 3;
+            xyz[3 * a + 0] = 2 * I + ((J + (c3 == 1)) & 1);
+            xyz[3 * a + 1] = 3 * J + c3;
+        } else {
+            xyz[3 * a + 0] = 2 * I + ((J + K) & 1);
+            xyz[3 * a + 1] = 3 * J + (K & 1);
+        }
         xyz[3 * a + 2] = K;
         if (ids) ids[a] = M->id;
     }

@@ -10,7 +10,9 @@
  * Paper: Miyauchi, Iwamoto, Arjunan, Takahashi, "pSpatiocyte: A Parallel
  * Stochastic Method for Particle Reaction-Diffusion Systems" (arXiv 1605.03726).
  *   Sec. 2.1      HCP lattice in twisted Cartesian coordinates (12 neighbours,
- *                 stencil chosen by the parity of the j and k layers).
+ *                 stencil chosen by the parity of the j and k layers); App. B
+ *                 (figures only) the FCC lattice in the same coordinates, ABC
+ *                 stacking (layer offsets chosen by k mod 3).
  *   Sec. 2.2      event scheduler: per-species diffusion events in time order.
  *   Sec. 2.3      diffusion: hop interval tau_d = 2 r_v^2 / (3 D); a molecule
  *                 moves to a randomly chosen neighbour only if it is vacant.
@@ -59,6 +61,8 @@ extern "C" {
 #define PSCO_PERIODIC_I 1u
 #define PSCO_PERIODIC_J 2u
 #define PSCO_PERIODIC_K 4u
+/* lattice flag bit: set = FCC (ABC stacking), clear = HCP (ABAB) */
+#define PSCO_FCC        8u
 
 typedef struct psco_lattice psco_lattice;
 
@@ -111,6 +115,7 @@ void psco_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
 int  psco_neighbor(const psco_lattice *L, int32_t i, int32_t j, int32_t k, int32_t d,
                    int32_t out_ijk[3], int32_t wrap[3]);   /* 1 = inside, 0 = wall */
 void psco_center(int32_t i, int32_t j, int32_t k, double xyz[3]);  /* units of r_v */
+void psco_center_fcc(int32_t i, int32_t j, int32_t k, double xyz[3]);   /* FCC lattice */
 
 #ifdef __cplusplus
 }

@@ -84,6 +84,8 @@ extern "C" {
 #define PSC_PERIODIC_J  2u       /* clear = reflective wall                    */
 #define PSC_PERIODIC_K  4u
 #define PSC_PERIODIC_ALL 7u
+#define PSC_FCC         8u       /* lattice flag: FCC (ABC stacking of the same
+                                    triangular layers, App. B) instead of HCP  */
 
 #define PSC_MAX_SPECIES    32
 #define PSC_MAX_REACTIONS 128
@@ -153,12 +155,23 @@ typedef struct {
 } psc_options;
 
 /*
- * Create an empty lattice (Sec. 2.1).
+ * Create an empty lattice (Sec. 2.1; FCC: App. B).
  *   ni, nj, nk       extents; a periodic i axis needs ni >= 3, a periodic j
  *                    (k) axis needs an even nj (nk) >= 4 so that the parity
- *                    stencil wraps consistently; ni * nj * nk < 2^31.
+ *                    stencil wraps consistently -- on the FCC lattice a
+ *                    periodic k axis needs nk >= 3 and a multiple of 3 (the
+ *                    stacking period); ni * nj * nk < 2^31.
  *   voxel_radius_m   r_v in metres (> 0).
- *   boundary_flags   PSC_PERIODIC_* bits.
+ *   boundary_flags   PSC_PERIODIC_* bits, plus PSC_FCC for the FCC lattice:
+ *                    the triangular layers stacked ABC, layer k at offset
+ *                    (0, 0), (1, 1/sqrt 3) or (0, 2/sqrt 3) r_v for k mod 3 =
+ *                    0, 1, 2 (row parity p = (j + [k mod 3 == 1]) & 1).  The
+ *                    twelve neighbours are the HCP ones in the layer; below,
+ *                    two at i-1+p, i+p on row j+a and one at (i, j+b) with
+ *                    (a, b) = (-1, 0) for k mod 3 = 0, else (0, +1); above,
+ *                    two on row j+a' and one at (i, j+b') with (a', b') =
+ *                    (+1, 0) for k mod 3 = 2, else (0, -1).  Stretches of
+ *                    FCC lattices use the molecule-list kernel.
  *   device           CUDA device ordinal.
  *   cuda_stream      cudaStream_t to queue work on, or NULL for a stream the
  *                    library creates and owns.
@@ -219,8 +232,8 @@ int psc_coords(psc_lattice *L, int32_t species, int32_t *ijk, uint32_t *ids,
 /* Unwrapped positions in the integer basis X = 2I + P, Y = 3J + (K & 1),
    Z = K, where I = i + wraps_i * ni (J, K likewise, wraps counted in 16 bits)
    and P = (J + K) & 1; the centre is (X, Y / sqrt 3, 2 sqrt(2/3) Z) r_v, so
-   squared displacements follow exactly (App. C, Eq. 14).  Sorted by id.
-   Synchronises. */
+   squared displacements follow exactly (App. C, Eq. 14).  FCC: Y = 3J +
+   (K mod 3), P = (J + [K mod 3 == 1]) & 1.  Sorted by id.  Synchronises. */
 int psc_unwrapped(psc_lattice *L, int32_t species, int32_t *xyz, uint32_t *ids,
                   int64_t cap, int64_t *n_out);
 

@@ -17,6 +17,7 @@ OK, E_ARG, E_DIMS, E_ORDER, E_FULL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
 W_PCLAMP = 1
 PERIODIC_I, PERIODIC_J, PERIODIC_K, PERIODIC_ALL = 1, 2, 4, 7
+FCC = 8                       # lattice flag: FCC (ABC stacking) instead of HCP
 MAX_SPECIES = 32
 
 _lib = None

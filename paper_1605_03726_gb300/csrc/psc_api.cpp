@@ -273,6 +273,7 @@ int enqueue_run(psc_lattice* L, int s, int n_events, int per_thread, int threads
 bool tile_plan(psc_lattice* L, int s, TilePlan* P)
 {
     if (L->opt.tiles < 0 || L->general[s] || L->live[s] || !(L->sp[s].D > 0.0)) return false;
+    if (L->bflags & PSC_FCC) return false;        // the boxes' stencil tables are the HCP ones
     if (L->opt.tiles == 0 && L->sp[s].n0 < ((int64_t)1 << 20)) return false;
     if (L->sp[s].n0 <= 0) return false;
     // periodic axes must wrap whole bricks
@@ -486,13 +487,14 @@ int psc_lattice_create(psc_lattice** out, int32_t ni, int32_t nj, int32_t nk, do
 {
     if (!out) return PSC_E_ARG;
     *out = nullptr;
-    if (!(rv > 0.0) || !std::isfinite(rv) || bflags > 7u || device < 0) return PSC_E_ARG;
+    if (!(rv > 0.0) || !std::isfinite(rv) || bflags > 15u || device < 0) return PSC_E_ARG;
     if (ni < 1 || nj < 1 || nk < 1) return PSC_E_DIMS;
     const int64_t V = (int64_t)ni * nj * nk;
     if (V >= (1ll << 31)) return PSC_E_DIMS;
     if ((bflags & PSC_PERIODIC_I) && ni < 3) return PSC_E_DIMS;
     if ((bflags & PSC_PERIODIC_J) && (nj < 4 || (nj & 1))) return PSC_E_DIMS;
-    if ((bflags & PSC_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSC_E_DIMS;
+    if (!(bflags & PSC_FCC) && (bflags & PSC_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSC_E_DIMS;
+    if ((bflags & PSC_FCC) && (bflags & PSC_PERIODIC_K) && (nk < 3 || nk % 3)) return PSC_E_DIMS;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) return PSC_E_CUDA;
     psc_lattice* L = new (std::nothrow) psc_lattice();
@@ -957,8 +959,14 @@ int psc_unwrapped(psc_lattice* L, int32_t s, int32_t* xyz, uint32_t* ids_out, in
         const int32_t I = i + (int32_t)(int16_t)(w & 0xFFFF) * L->ni;
         const int32_t J = j + (int32_t)(int16_t)((w >> 16) & 0xFFFF) * L->nj;
         const int32_t K = k + (int32_t)(int16_t)((w >> 32) & 0xFFFF) * L->nk;
-        xyz[3 * a + 0] = 2 * I + ((J + K) & 1);
-        xyz[3 * a + 1] = 3 * J + (K & 1);
+        if (L->bflags & PSC_FCC) {
+            const int32_t c3 = ((K % 3) + 3) % 3;
+            xyz[3 * a + 0] = 2 * I + ((J + (c3 == 1 ? 1 : 0)) & 1);
+            xyz[3 * a + 1] = 3 * J + c3;
+        } else {
+            xyz[3 * a + 0] = 2 * I + ((J + K) & 1);
+            xyz[3 * a + 1] = 3 * J + (K & 1);
+        }
         xyz[3 * a + 2] = K;
         if (ids_out) ids_out[a] = ids[order[a]];
     }

@@ -41,7 +41,11 @@ namespace psc {
 // Words: [0] di for p = 0, [1] di for p = 1, [2] dj for even k, [3] dj for odd
 // k, [4] dk.  Every warp reads all five words (uniform addresses), then picks
 // per thread, so the constant cache serves them as broadcasts.
-__constant__ uint32_t c_stencil[5];
+// FCC lattice (App. B; ABC stacking, c = k mod 3, p = (j + [c == 1]) & 1):
+// the same di and dk words; dj from words [5 + c]:
+//   d 6, 7: a = -1 for c = 0, else 0     d 8:  b = 0 for c = 0, else +1
+//   d 9,10: a' = +1 for c = 2, else 0    d 11: b' = 0 for c = 2, else -1
+__constant__ uint32_t c_stencil[8];
 
 static uint32_t pack_offsets(const int (&o)[12])
 {
@@ -57,10 +61,14 @@ void upload_stencil(cudaStream_t st)
     const int dj0[12] = {0, 0, -1, -1, +1, +1, 0, 0, -1, 0, 0, -1};
     const int dj1[12] = {0, 0, -1, -1, +1, +1, 0, 0, +1, 0, 0, +1};
     const int dk[12] = {0, 0, 0, 0, 0, 0, -1, -1, -1, +1, +1, +1};
-    static uint32_t h[5];
+    const int fj0[12] = {0, 0, -1, -1, +1, +1, -1, -1, 0, 0, 0, -1};
+    const int fj1[12] = {0, 0, -1, -1, +1, +1, 0, 0, +1, 0, 0, -1};
+    const int fj2[12] = {0, 0, -1, -1, +1, +1, 0, 0, +1, +1, +1, 0};
+    static uint32_t h[8];
     h[0] = pack_offsets(di0); h[1] = pack_offsets(di1);
     h[2] = pack_offsets(dj0); h[3] = pack_offsets(dj1);
     h[4] = pack_offsets(dk);
+    h[5] = pack_offsets(fj0); h[6] = pack_offsets(fj1); h[7] = pack_offsets(fj2);
     cudaMemcpyToSymbolAsync(c_stencil, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
 }
 
@@ -154,8 +162,16 @@ __device__ __forceinline__ bool neighbor(const Geometry& G, int32_t i, int32_t j
 {
     const uint32_t s0 = c_stencil[0], s1 = c_stencil[1], s2 = c_stencil[2], s3 = c_stencil[3],
                    s4 = c_stencil[4];
-    const uint32_t wi = ((j + k) & 1) ? s1 : s0;
-    const uint32_t wj = (k & 1) ? s3 : s2;
+    uint32_t wi, wj;
+    if (G.bflags & 8u) {                          // FCC
+        const int c = k % 3;
+        const uint32_t f0 = c_stencil[5], f1 = c_stencil[6], f2 = c_stencil[7];
+        wi = ((j + (c == 1 ? 1 : 0)) & 1) ? s1 : s0;
+        wj = c == 0 ? f0 : (c == 1 ? f1 : f2);
+    } else {
+        wi = ((j + k) & 1) ? s1 : s0;
+        wj = (k & 1) ? s3 : s2;
+    }
     int32_t ti = i + (int32_t)((wi >> (2 * d)) & 3u) - 1;
     int32_t tj = j + (int32_t)((wj >> (2 * d)) & 3u) - 1;
     int32_t tk = k + (int32_t)((s4 >> (2 * d)) & 3u) - 1;

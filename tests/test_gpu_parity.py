@@ -269,3 +269,32 @@ def test_tile_kernel_interleaved_species_with_crowders(claim_table):
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, chunk)
+
+
+# FCC lattice (App. B): the per-event kernels (reactions), the molecule-list
+# persistent kernel (walkers), periodic with k a multiple of 3 and reflective
+# ragged shapes; the tile kernel does not take FCC and must fall back.
+FCC_CASES = [
+    ((24, 24, 24), psc.PERIODIC_ALL | psc.FCC, "ab"),
+    ((48, 40, 30), psc.PERIODIC_ALL | psc.FCC, "walk"),
+    ((37, 29, 23), psc.FCC, "walk"),
+    ((30, 28, 27), psc.FCC, "crowded"),
+    ((24, 20, 18), psc.PERIODIC_ALL | psc.FCC, "mapk"),
+]
+
+
+@pytest.mark.parametrize("persistent", [1, -1])
+@pytest.mark.parametrize("shape,boundary,model", FCC_CASES)
+def test_fcc_lattice_matches_oracle(shape, boundary, model, persistent):
+    V = shape[0] * shape[1] * shape[2]
+    recipe = {
+        "ab": lambda L: models.reaction_diffusion_ab(L, 600, 500, k=5e-19),
+        "walk": lambda L: models.diffusion_only(L, int(0.1 * V)),
+        "crowded": lambda L: models.crowded_reversible(L, V, kb=2000.0),
+        "mapk": lambda L: models.mapk_like(L, 5, scale=0.1, uni_scale=300, bi_scale=3),
+    }[model]
+    g, o = build_both(shape, recipe, 13, boundary=boundary, persistent=persistent, tiles=1)
+    for chunk in (3, 30, 90):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)

@@ -70,3 +70,35 @@ def test_512cubed_long_run_properties():
     assert set(np.unique(d).tolist()) <= {0, 12}
     assert int(np.count_nonzero(d)) == L.stats()["hops"] - h0
     L.close()
+
+
+def test_fcc_long_run_properties():
+    # FCC lattice (App. B), 192^3 periodic, 1 % walkers, 500 events: exclusion,
+    # one-diameter hops, MSD = (2 r_v)^2 x hops, isotropic second moment
+    shape = (192, 192, 192)
+    n = int(0.01 * shape[0] * shape[1] * shape[2])
+    L = psc.Lattice(*shape, voxel_radius=RV, boundary=psc.PERIODIC_ALL | psc.FCC)
+    s = L.add_species(D, n)
+    L.set_options(collect_stats=1)
+    L.populate(2)
+    x0, id0 = L.unwrapped(s)
+    L.run_events(500)
+    st = L.stats()
+    ijk, ids = L.coords(s)
+    assert np.array_equal(ids, id0)
+    v = ijk[:, 0].astype(np.int64) + shape[0] * (ijk[:, 1] + shape[1] * ijk[:, 2].astype(np.int64))
+    assert np.unique(v).size == n
+    assert int(np.count_nonzero(L.grid())) == n
+    x1, _ = L.unwrapped(s)
+    a = axes3(x0, x1)
+    ratio = a.sum(axis=1).mean() / (12.0 * st["hops"] / n)
+    assert 0.985 < ratio < 1.01, ratio
+    share = a.mean(axis=0) / a.sum(axis=1).mean()
+    assert np.allclose(share, 1.0 / 3.0, atol=0.01), share
+    h0 = L.stats()["hops"]
+    L.run_events(1)
+    x2, _ = L.unwrapped(s)
+    d = axes3(x1, x2).sum(axis=1)
+    assert set(np.unique(d).tolist()) <= {0, 12}
+    assert int(np.count_nonzero(d)) == L.stats()["hops"] - h0
+    L.close()

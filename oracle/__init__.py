@@ -12,7 +12,7 @@ from .build import build as _build
 
 OK, E_ARG, E_DIMS, E_ORDER, E_FULL, E_UNSUPPORTED, E_NOMEM, E_LIMIT = 0, -1, -2, -3, -4, -5, -6, -9
 W_PCLAMP = 1
-RULE_SYNC, RULE_SEQ_ID, RULE_SEQ_RANDOM = 0, 1, 2
+RULE_SYNC, RULE_SEQ_ID, RULE_SEQ_RANDOM, RULE_SUBVOL = 0, 1, 2, 3
 PERIODIC_I, PERIODIC_J, PERIODIC_K = 1, 2, 4
 PERIODIC_ALL = 7
 FCC = 8                  # lattice flag: FCC (ABC stacking) instead of HCP

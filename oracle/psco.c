@@ -53,6 +53,7 @@ void psco_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
 #define TAG_EVENT    0u
 #define TAG_POPULATE 1u
 #define TAG_ORDER    2u
+#define TAG_SUBVOL   3u
 
 static void draw(const psco_lattice *L, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t u[4]);
 
@@ -270,7 +271,7 @@ int psco_lattice_create(psco_lattice **out, int32_t ni, int32_t nj, int32_t nk,
     if (!out) return PSCO_E_ARG;
     *out = NULL;
     if (!(rv > 0.0) || !isfinite(rv) || bflags > 15u) return PSCO_E_ARG;
-    if (rule < PSCO_RULE_SYNC || rule > PSCO_RULE_SEQ_RANDOM) return PSCO_E_ARG;
+    if (rule < PSCO_RULE_SYNC || rule > PSCO_RULE_SUBVOL) return PSCO_E_ARG;
     if (ni < 1 || nj < 1 || nk < 1) return PSCO_E_DIMS;
     int64_t V = (int64_t)ni * nj * nk;
     if (V >= ((int64_t)1 << 31)) return PSCO_E_DIMS;
@@ -280,6 +281,10 @@ int psco_lattice_create(psco_lattice **out, int32_t ni, int32_t nj, int32_t nk,
     if ((bflags & PSCO_PERIODIC_J) && (nj < 4 || (nj & 1))) return PSCO_E_DIMS;
     if (!(bflags & PSCO_FCC) && (bflags & PSCO_PERIODIC_K) && (nk < 4 || (nk & 1))) return PSCO_E_DIMS;
     if ((bflags & PSCO_FCC) && (bflags & PSCO_PERIODIC_K) && (nk < 3 || nk % 3)) return PSCO_E_DIMS;
+    /* sub-volume colours must alternate across a periodic wrap */
+    if (rule == PSCO_RULE_SUBVOL && (((bflags & PSCO_PERIODIC_I) && ni % 4) || ((bflags & PSCO_PERIODIC_J) && nj % 4) ||
+                                     ((bflags & PSCO_PERIODIC_K) && nk % 4)))
+        return PSCO_E_DIMS;
     psco_lattice *L = (psco_lattice *)calloc(1, sizeof(psco_lattice));
     if (!L) return PSCO_E_NOMEM;
     L->ni = ni; L->nj = nj; L->nk = nk; L->V = V;
@@ -767,6 +772,56 @@ static int event_seq(psco_lattice *L, int32_t s, uint32_t g, int random_order)
     return rc;
 }
 
+/* the paper's sub-volume scheme (Sec. 2.5: sub-volumes are taken one after
+   another in a random order, so that those processed at the same time never
+   touch each other), on the lattice: sub-volumes of 2 x 2 x 2 voxels, colour
+   = parities of the sub-volume indices (i/2, j/2, k/2).  Sub-volumes of one
+   colour are at least one sub-volume apart, so a hop (one voxel) from one of
+   them never reaches what a hop from another reads or writes.  The event's
+   colour order is a Fisher-Yates shuffle of 0..7 with draw (a, g, s<<4 |
+   TAG_SUBVOL) for a = 7..1; each colour takes, in ascending id, the molecules
+   of the species standing in its sub-volumes that the event has not yet
+   processed, each seeing the grid as left before it. */
+static int subvol_colour(const psco_lattice *L, int64_t v)
+{
+    int32_t c[3];
+    decode(L, v, c);
+    return ((c[0] >> 1) & 1) | (((c[1] >> 1) & 1) << 1) | (((c[2] >> 1) & 1) << 2);
+}
+
+static int event_subvol(psco_lattice *L, int32_t s, uint32_t g)
+{
+    int rc = rebuild_list(L, s);
+    if (rc) return rc;
+    int64_t n = L->sp[s].nlist;
+    if (n == 0) return PSCO_OK;
+    int64_t *order = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    unsigned char *done = (unsigned char *)calloc((size_t)n, 1);
+    if (!order || !done) { free(order); free(done); return PSCO_E_NOMEM; }
+    memcpy(order, L->sp[s].list, (size_t)n * sizeof(int64_t));
+    int colours[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+    for (int a = 7; a > 0; --a) {
+        uint32_t u[4];
+        draw(L, (uint32_t)a, g, ((uint32_t)s << 4) | TAG_SUBVOL, u);
+        int b = (int)(((uint64_t)u[0] * (uint64_t)(a + 1)) >> 32);
+        int tmp = colours[a]; colours[a] = colours[b]; colours[b] = tmp;
+    }
+    for (int ci = 0; ci < 8 && rc == PSCO_OK; ++ci) {
+        for (int64_t a = 0; a < n && rc == PSCO_OK; ++a) {
+            if (done[a] || subvol_colour(L, L->mol[order[a]].v) != colours[ci]) continue;
+            done[a] = 1;
+            intent it;
+            decide(L, s, g, order[a], &it);
+            birth b; int hb = 0;
+            apply(L, s, &it, &b, &hb);
+            if (hb) rc = place_birth(L, &b, L->next_id++);
+        }
+    }
+    free(order);
+    free(done);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* event scheduler (Sec. 2.2): the next event is the mobile species with the  */
 /* earliest next diffusion time (events_done + 1) * tau; ties go to the lower  */
@@ -791,6 +846,7 @@ static int do_event(psco_lattice *L, int32_t s)
     if (L->g == UINT32_MAX) return PSCO_E_LIMIT;
     int rc;
     if (L->rule == PSCO_RULE_SYNC) rc = event_sync(L, s, L->g);
+    else if (L->rule == PSCO_RULE_SUBVOL) rc = event_subvol(L, s, L->g);
     else rc = event_seq(L, s, L->g, L->rule == PSCO_RULE_SEQ_RANDOM);
     if (rc) return rc;
     L->sp[s].done++;

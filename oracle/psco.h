@@ -28,7 +28,14 @@
  *   PSCO_RULE_SEQ_ID      the paper's one-by-one update (Sec. 2.3) in ascending
  *                         id order, each molecule seeing the current grid.
  *   PSCO_RULE_SEQ_RANDOM  the same, in a fresh random order every event.
- * All three use the same per-molecule draws.
+ *   PSCO_RULE_SUBVOL      the paper's sub-volume scheme (Sec. 2.5) on the
+ *                         lattice: 2 x 2 x 2-voxel sub-volumes coloured by the
+ *                         parities of their indices; each event takes the eight
+ *                         colours in an order drawn for it, and within a colour
+ *                         the molecules standing in sub-volumes of that colour,
+ *                         not yet processed in the event, one by one in
+ *                         ascending id, each seeing the current grid.
+ * All use the same per-molecule draws.
  */
 #ifndef PSCO_H
 #define PSCO_H
@@ -53,6 +60,7 @@ extern "C" {
 #define PSCO_RULE_SYNC        0
 #define PSCO_RULE_SEQ_ID      1
 #define PSCO_RULE_SEQ_RANDOM  2
+#define PSCO_RULE_SUBVOL      3   /* periodic axes need extents that are multiples of 4 */
 
 #define PSCO_MAX_SPECIES    64
 #define PSCO_MAX_REACTIONS 256

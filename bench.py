@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--replicas", type=int, default=512, help="replicas of the serving workload")
     ap.add_argument("--serial-sample", type=int, default=16, help="replicas timed one at a time")
+    ap.add_argument("--rule", default="sync", choices=["sync", "subvolume"],
+                    help="update rule: synchronous claims (the paper's hot path on the GPU), or the "
+                         "sub-volume colouring rule (Sec. 2.5), for comparison")
     return ap.parse_args()
 
 
@@ -203,10 +206,12 @@ def profiled_traffic(name):
         return None
 
 
-def make_lattice(psc, seed, device, stream):
+def make_lattice(psc, seed, device, stream, rule="sync"):
     L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=device, stream=stream)
     L.add_species(D, N_MOL)
     L.set_options(resort_period=RESORT_PERIOD)
+    if rule == "subvolume":
+        L.set_options(subvolume=1)
     L.populate(seed)
     return L
 
@@ -220,7 +225,7 @@ def gpu_arm(args, rank, world, local):
     ranks = Ranks(rank, world, "nccl", local)
     barrier = ranks.barrier
     stream = torch.cuda.Stream(device=local)
-    L = make_lattice(psc, replica_seed(rank), local, stream.cuda_stream)
+    L = make_lattice(psc, replica_seed(rank), local, stream.cuda_stream, args.rule)
 
     # warm-up
     for _ in range(args.warmup):
@@ -273,7 +278,7 @@ def gpu_arm(args, rank, world, local):
     tr = profiled_traffic("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
     traffic = None
     events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
-    if persistent and tr and tr.get("kernel_rev") == kernel_revision() and \
+    if persistent and args.rule == "sync" and tr and tr.get("kernel_rev") == kernel_revision() and \
             int(tr.get("events_per_launch", 0)) == round(events_per_launch):
         traffic = int(tr["dram_read_bytes"]) + int(tr["dram_write_bytes"])
     roofline = {
@@ -283,7 +288,9 @@ def gpu_arm(args, rank, world, local):
                                                                           else "hop_run_512cubed"),
         "events_per_launch": events_per_launch,
         "bytes_alg_per_launch": round(b_alg * N_MOL * events_per_launch),
-        "kernel": ("k_tile_run (owner-computes boxes in shared memory, neighbour waits; one launch per stretch, "
+        "kernel": ("k_subvol_run (sub-volume rule: eight colour passes per event, rounds per colour)"
+                   if args.rule == "subvolume" else
+                   "k_tile_run (owner-computes boxes in shared memory, neighbour waits; one launch per stretch, "
                    "with k_tile_scatter / k_tile_gather)" if tiles_used
                    else "k_hop_run (persistent: claim phase, grid barrier, commit phase per event)" if persistent
                    else "k_claim + k_commit (one hop event over all molecules)"),
@@ -324,6 +331,8 @@ def e2e_run(psc, args, rank, local, torch, ranks):
     L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=local)
     L.add_species(D, N_MOL)
     L.set_options(resort_period=RESORT_PERIOD)
+    if args.rule == "subvolume":
+        L.set_options(subvolume=1)
     L.populate(replica_seed(rank))
     for _ in range(args.steps):
         L.run_events(EVENTS_PER_STEP)
@@ -513,7 +522,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["elapsed_ms"] / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": list(SHAPE), "molecules": N_MOL,
+        "config": {"workload": WORKLOAD if args.rule == "sync" else WORKLOAD + "; sub-volume update rule",
+                   "rule": args.rule, "lattice": list(SHAPE), "molecules": N_MOL,
                    "events_per_step": EVENTS_PER_STEP, "resort_period": RESORT_PERIOD,
                    "replicas": world, "l2": "inputs larger than L2 (occupancy 268 MB + claim words 537 MB)",
                    "parallelism": "replicas (one independent lattice per GPU)"},

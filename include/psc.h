@@ -152,6 +152,17 @@ typedef struct {
                                  (when the species has >= 2^20 molecules)      */
     int32_t tile_regions;     /* tile kernel: most boxes (blocks) to cut the
                                  lattice into (0/-1 = one per SM)              */
+    int32_t subvolume;        /* before populate: 1 = update rule of the
+                                 paper's sub-volume scheme (Sec. 2.5) instead
+                                 of the synchronous rule: 2x2x2-voxel
+                                 sub-volumes in eight colours taken in an
+                                 order drawn per event (draws (a, g, s<<4 | 3),
+                                 a = 7..1, Fisher-Yates), sequential in
+                                 ascending id within a colour, each molecule
+                                 once per event.  Species without reactions
+                                 only (else PSC_E_UNSUPPORTED at populate);
+                                 periodic extents must be multiples of 4
+                                 (PSC_E_DIMS).  -1 = synchronous (default)     */
 } psc_options;
 
 /*

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
         "claim_table", "persistent", "slot_map", "claim_slots", "run_per_thread", "barrier_timeout_us", "barrier_phantom", "tiles",
-        "tile_regions")]
+        "tile_regions", "subvolume")]
 
 
 class KernelTimes(ctypes.Structure):

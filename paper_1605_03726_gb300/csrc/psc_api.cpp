@@ -415,6 +415,34 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     return cuda_fail(L, cudaPeekAtLastError());
 }
 
+// the sub-volume rule: one cooperative launch over a stretch of events
+int enqueue_subvol(psc_lattice* L, int s, int64_t n_events)
+{
+    cudaStream_t st = L->stream;
+    SubvolArgs A{};
+    A.ev = event_args(L, s);
+    A.word[0] = L->subvol.word[0];
+    A.word[1] = L->subvol.word[1];
+    A.done = L->subvol.done;
+    A.won = L->subvol.won;
+    A.alone = L->subvol.alone;
+    A.count = L->subvol.count;
+    A.n_events = (int32_t)n_events;
+    A.barrier = L->barrier;
+    A.barrier_timeout_ns = (uint64_t)L->opt.barrier_timeout_us * 1000ull;
+    A.barrier_phantom = (uint32_t)L->opt.barrier_phantom;
+    int rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st));
+    if (rc) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->subvol.count, 0, 3 * sizeof(uint32_t), st)))) return rc;
+    cudaEvent_t sp = span_open(L);
+    rc = cuda_fail(L, launch_subvol(A, L->subvol.blocks, 256, st));
+    span_close(L, sp, kSpanRun, n_events);
+    if (rc) return rc;
+    L->launches += 1;
+    L->events += (uint64_t)n_events;
+    return PSC_OK;
+}
+
 // Sec. 2.2: the next event belongs to the mobile species whose next diffusion
 // time (events done + 1) * tau is earliest; ties go to the lower index.
 bool next_event(const psc_lattice* L, int* s_out, double* t_out)
@@ -653,6 +681,14 @@ int psc_populate(psc_lattice* L, uint64_t seed)
             for (int r = 0; r < L->nsp; ++r) if (L->pair[s][r] >= 0) L->reconcile[s].push_back(r);
         }
     }
+    // ---- the sub-volume rule takes species without reactions on colour-consistent periods ----
+    if (L->opt.subvolume > 0) {
+        for (int s = 0; s < L->nsp; ++s)
+            if (L->sp[s].D > 0.0 && L->general[s]) return PSC_E_UNSUPPORTED;
+        if (((L->bflags & PSC_PERIODIC_I) && L->ni % 4) || ((L->bflags & PSC_PERIODIC_J) && L->nj % 4) ||
+            ((L->bflags & PSC_PERIODIC_K) && L->nk % 4))
+            return PSC_E_DIMS;
+    }
     // ---- capacities: a list only grows if its species is a product ----
     const int64_t total_bound = growth ? L->V : N;
     int64_t max_cap = 1, max_mobile = 1;
@@ -731,6 +767,25 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     if (!L->births || !L->rs_keys || !L->rs_vals || !rs) return PSC_E_NOMEM;
     sort_scratch_bind(L->rs_scratch, rs, max_mobile);
 
+    if (L->opt.subvolume > 0) {
+        auto& SV = L->subvol;
+        const size_t nsub = (size_t)((L->ni + 1) / 2) * (size_t)((L->nj + 1) / 2) * (size_t)((L->nk + 1) / 2);
+        SV.word[0] = (uint32_t*)dev_alloc(L, nsub * 4);
+        SV.word[1] = (uint32_t*)dev_alloc(L, nsub * 4);
+        SV.done = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.won = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.alone = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.count = (uint32_t*)dev_alloc(L, 16);
+        if (!SV.word[0] || !SV.word[1] || !SV.done || !SV.won || !SV.alone || !SV.count) return PSC_E_NOMEM;
+        SV.blocks = subvol_max_blocks(L->sm_count);
+        if (SV.blocks <= 0) return PSC_E_CUDA;
+        launch_fill_u32(SV.word[0], kNoClaim, nsub, L->sm_count * 4, L->stream);
+        launch_fill_u32(SV.word[1], kNoClaim, nsub, L->sm_count * 4, L->stream);
+        int rcs;
+        if ((rcs = cuda_fail(L, cudaMemsetAsync(SV.done, 0, (size_t)max_mobile * 4, L->stream)))) return rcs;
+        if ((rcs = cuda_fail(L, cudaMemsetAsync(SV.won, 0, (size_t)max_mobile * 4, L->stream)))) return rcs;
+    }
+
     cudaStream_t st = L->stream;
     upload_stencil(st);
     int rc = cuda_fail(L, cudaMemcpyAsync(L->model_d, &M, sizeof(M), cudaMemcpyHostToDevice, st));
@@ -790,6 +845,31 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
         double t;
         if (!next_event(L, &s, &t) || t > t_end) break;
         if (L->g == UINT32_MAX) return PSC_E_LIMIT;
+        if (L->opt.subvolume > 0) {
+            // the sub-volume rule: stretches of the species' events, one launch each
+            const uint32_t g0 = L->g;
+            const int64_t limit = std::max<int64_t>(
+                1, std::min<int64_t>(std::min<int64_t>(max_events - queued, (int64_t)1 << 16),
+                                     (int64_t)UINT32_MAX - L->g));
+            int64_t e = 0;
+            for (;;) {
+                L->sp[s].done++;
+                L->g++;
+                L->clock = t;
+                ++e;
+                if (e >= limit) break;
+                int s2;
+                double t2;
+                if (!next_event(L, &s2, &t2) || s2 != s || t2 > t_end) break;
+                t = t2;
+            }
+            L->g = g0;
+            int rc = enqueue_subvol(L, s, e);
+            L->g = g0 + (uint32_t)e;
+            if (rc) return rc;
+            queued += e;
+            continue;
+        }
         int threads = 0, blocks = 0;
         const int per = run_width(L, s, &threads, &blocks);
         TilePlan plan{};
@@ -1063,6 +1143,10 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
     }
     if (o->barrier_phantom) L->opt.barrier_phantom = o->barrier_phantom < 0 ? 0 : o->barrier_phantom;
     if (o->tiles) L->opt.tiles = o->tiles > 0 ? 1 : -1;
+    if (o->subvolume) {
+        if (L->populated) return PSC_E_ORDER;
+        L->opt.subvolume = o->subvolume > 0 ? 1 : -1;
+    }
     if (o->tile_regions) L->opt.tile_regions = o->tile_regions < 0 ? 0 : o->tile_regions;
     if (o->slot_map) {
         if (o->slot_map < 1 || o->slot_map > 3) return PSC_E_ARG;

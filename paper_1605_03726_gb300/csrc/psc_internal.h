@@ -195,6 +195,21 @@ struct TileArgs {
     uint32_t barrier_phantom;
 };
 
+// A stretch of events of one species under the sub-volume rule (the paper's
+// sub-volume scheme on the lattice; species without reactions).
+struct SubvolArgs {
+    EventArgs ev;              // g = index of the first event
+    uint32_t* word[2];         // per 2x2x2 sub-volume: lowest id still to go (by round parity)
+    uint32_t* done;            // per list slot: 1 + index of the event that processed it
+    uint32_t* won;             // per list slot: 1 + sub-volume it won last round (its word is reset next round)
+    uint32_t* alone;           // per list slot: alone in its sub-volume at the round's phase A
+    uint32_t* count;           // [3] candidates per round, rotating
+    int32_t n_events;
+    BarrierState* barrier;
+    uint64_t barrier_timeout_ns;
+    uint32_t barrier_phantom;
+};
+
 struct ReconcileArgs {
     Geometry geo;
     uint16_t* occ;
@@ -215,6 +230,8 @@ void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStre
 // stretch does not fit); threads = its launch width.
 int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count, int min_per_thread);
 cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread, cudaStream_t st);
+cudaError_t launch_subvol(const SubvolArgs& A, int blocks, int threads, cudaStream_t st);
+int subvol_max_blocks(int sm_count);        // co-resident 256-thread blocks of the sub-volume kernel
 // tile kernel: dynamic shared memory a block may use, its need for a plan,
 // the three launches of a stretch (list -> buckets, the persistent events,
 // buckets -> list)

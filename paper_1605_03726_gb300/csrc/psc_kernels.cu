@@ -1293,5 +1293,6 @@ void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStrea
 }
 
 #include "psc_tiles.cuh"
+#include "psc_subvol.cuh"
 
 }  // namespace psc

@@ -82,7 +82,7 @@ struct psc_lattice {
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3, 0, 1000000, 0, 0, 0};
+    psc_options opt{64, 256, 8, 0, 0, 0, 0, 1, 1, 3, 0, 1000000, 0, 0, 0, -1};
     int64_t launches = 0;
     uint64_t events = 0;
     uint64_t h2d = 0, d2h = 0;
@@ -112,6 +112,16 @@ struct psc_lattice {
         uint32_t* claim = nullptr;     // per-voxel claim words when the lattice has none
     } tile;
     int tile_smem = -1;                // shared memory a tile block may use (-1: not queried yet)
+
+    // sub-volume rule buffers (allocated at populate when the rule is on)
+    struct SubvolBuffers {
+        uint32_t* word[2] = {nullptr, nullptr};
+        uint32_t* done = nullptr;
+        uint32_t* won = nullptr;
+        uint32_t* alone = nullptr;
+        uint32_t* count = nullptr;
+        int blocks = 0;
+    } subvol;
 };
 
 namespace psc_rt {
@@ -137,5 +147,6 @@ void dev_free_one(psc_lattice* L, void* p);
 // Can stretches of species s run under the tile kernel?  Fills the plan.
 bool tile_plan(psc_lattice* L, int s, TilePlan* P);
 int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P);
+int enqueue_subvol(psc_lattice* L, int s, int64_t n_events);
 
 }  // namespace psc_rt

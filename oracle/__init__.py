@@ -11,6 +11,7 @@ import numpy as np
 from .build import build as _build
 
 OK, E_ARG, E_DIMS, E_ORDER, E_FULL, E_UNSUPPORTED, E_NOMEM, E_LIMIT = 0, -1, -2, -3, -4, -5, -6, -9
+MAX_COMPARTMENTS = 16
 W_PCLAMP = 1
 RULE_SYNC, RULE_SEQ_ID, RULE_SEQ_RANDOM, RULE_SUBVOL = 0, 1, 2, 3
 PERIODIC_I, PERIODIC_J, PERIODIC_K = 1, 2, 4
@@ -41,6 +42,8 @@ def lib():
             "psco_lattice_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, i32, dbl, u32, i32]),
             "psco_add_species": (ctypes.c_int, [P, dbl, i64, ctypes.POINTER(i32)]),
             "psco_add_reaction": (ctypes.c_int, [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32, dbl, ctypes.POINTER(i32)]),
+            "psco_set_compartments": (ctypes.c_int, [P, P, i32]),
+            "psco_species_compartment": (ctypes.c_int, [P, i32, i32]),
             "psco_populate": (ctypes.c_int, [P, u64]),
             "psco_run": (ctypes.c_int, [P, dbl]),
             "psco_run_events": (ctypes.c_int, [P, i64]),
@@ -132,10 +135,12 @@ class Lattice:
         except Exception:
             pass
 
-    def add_species(self, D, count):
+    def add_species(self, D, count, compartment=None):
         s = ctypes.c_int32()
         _check("psco_add_species", lib().psco_add_species(self._h, float(D), int(count), ctypes.byref(s)))
         self.n_species += 1
+        if compartment is not None:
+            self.species_compartment(s.value, compartment)
         return s.value
 
     def add_reaction(self, reactants, products, k):
@@ -145,6 +150,14 @@ class Lattice:
         _check("psco_add_reaction", lib().psco_add_reaction(
             self._h, r, len(reactants), p, len(products), float(k), ctypes.byref(out)))
         return out.value
+
+    def set_compartments(self, labels, n):
+        """labels: uint8 per voxel, flat (v = i + ni (j + nj k)) or shaped (nk, nj, ni)."""
+        lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+        _check("psco_set_compartments", lib().psco_set_compartments(self._h, _ptr(lab), int(n)))
+
+    def species_compartment(self, species, c):
+        _check("psco_species_compartment", lib().psco_species_compartment(self._h, species, int(c)))
 
     def populate(self, seed):
         return _check("psco_populate", lib().psco_populate(self._h, int(seed)), (OK, W_PCLAMP))

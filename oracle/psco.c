@@ -79,6 +79,7 @@ typedef struct {
     int64_t *list;       /* indices into mol[] (rebuilt when dirty)  */
     int64_t  nlist;
     int      dirty;
+    int32_t  comp;       /* compartment the species lives in (Sec. 2) */
 } ospec;
 
 typedef struct {
@@ -101,6 +102,8 @@ struct psco_lattice {
     orx      rx[PSCO_MAX_REACTIONS];
     int16_t  pair[PSCO_MAX_SPECIES][PSCO_MAX_SPECIES];
     uint16_t *occ;       /* 0 vacant, s+1 species s                  */
+    uint8_t  *comp;      /* compartment of every voxel, NULL = all 0 */
+    int32_t  ncomp;
     int64_t  *who;       /* voxel -> index into mol[], -1 if vacant  */
     omol     *mol;
     int64_t  nmol, capmol;
@@ -222,6 +225,13 @@ static void decode(const psco_lattice *L, int64_t v, int32_t ijk[3])
     ijk[2] = (int32_t)(v / ((int64_t)L->ni * L->nj));
 }
 
+/* compartment of voxel v (Sec. 2: a cell is a set of compartments, each a
+   group of voxels) */
+static int32_t vcomp(const psco_lattice *L, int64_t v)
+{
+    return L->comp ? (int32_t)L->comp[v] : 0;
+}
+
 static int64_t encode(const psco_lattice *L, const int32_t ijk[3])
 {
     return (int64_t)ijk[0] + (int64_t)L->ni * ((int64_t)ijk[1] + (int64_t)L->nj * ijk[2]);
@@ -289,6 +299,7 @@ int psco_lattice_create(psco_lattice **out, int32_t ni, int32_t nj, int32_t nk,
     if (!L) return PSCO_E_NOMEM;
     L->ni = ni; L->nj = nj; L->nk = nk; L->V = V;
     L->rv = rv; L->bflags = bflags; L->rule = rule;
+    L->ncomp = 1;
     for (int a = 0; a < PSCO_MAX_SPECIES; ++a)
         for (int b = 0; b < PSCO_MAX_SPECIES; ++b)
             L->pair[a][b] = -1;
@@ -350,11 +361,63 @@ int psco_add_reaction(psco_lattice *L, const int32_t *re, int32_t nr,
     return PSCO_OK;
 }
 
+/* compartments (Sec. 2): labels[v] for v = i + ni (j + nj k), each below n */
+int psco_set_compartments(psco_lattice *L, const uint8_t *labels, int32_t n)
+{
+    if (!L || !labels) return PSCO_E_ARG;
+    if (L->populated) return PSCO_E_ORDER;
+    if (n < 1 || n > PSCO_MAX_COMPARTMENTS) return PSCO_E_ARG;
+    for (int64_t v = 0; v < L->V; ++v)
+        if (labels[v] >= n) return PSCO_E_ARG;
+    for (int s = 0; s < L->nsp; ++s)
+        if (L->sp[s].comp >= n) return PSCO_E_ARG;
+    uint8_t *c = (uint8_t *)malloc((size_t)L->V);
+    if (!c) return PSCO_E_NOMEM;
+    memcpy(c, labels, (size_t)L->V);
+    free(L->comp);
+    L->comp = c;
+    L->ncomp = n;
+    return PSCO_OK;
+}
+
+int psco_species_compartment(psco_lattice *L, int32_t s, int32_t c)
+{
+    if (!L || s < 0 || s >= L->nsp) return PSCO_E_ARG;
+    if (L->populated) return PSCO_E_ORDER;
+    if (c < 0 || c >= L->ncomp) return PSCO_E_ARG;
+    L->sp[s].comp = c;
+    return PSCO_OK;
+}
+
+/* Reactions must leave every product in its own compartment, given where the
+   products go: a first-order product that stays keeps the reactant's voxel;
+   a second-order reaction puts its products on the two reactants' voxels. */
+static int reactions_fit_compartments(const psco_lattice *L)
+{
+    for (int r = 0; r < L->nrx; ++r) {
+        const orx *R = &L->rx[r];
+        int32_t ca = L->sp[R->r[0]].comp;
+        if (R->nr == 1) {
+            if (R->np >= 1 && L->sp[R->p[0]].comp != ca) return 0;
+            continue;
+        }
+        int32_t cb = L->sp[R->r[1]].comp;
+        if (R->np == 1) {
+            int32_t c0 = L->sp[R->p[0]].comp;
+            if (c0 != ca && c0 != cb) return 0;
+        } else if (R->np == 2) {
+            int32_t c0 = L->sp[R->p[0]].comp, c1 = L->sp[R->p[1]].comp;
+            if (!((c0 == ca && c1 == cb) || (c0 == cb && c1 == ca))) return 0;
+        }
+    }
+    return 1;
+}
+
 void psco_lattice_destroy(psco_lattice *L)
 {
     if (!L) return;
     for (int s = 0; s < L->nsp; ++s) free(L->sp[s].list);
-    free(L->occ); free(L->who); free(L->mol);
+    free(L->occ); free(L->who); free(L->mol); free(L->comp);
     free(L);
 }
 
@@ -460,6 +523,15 @@ int psco_populate(psco_lattice *L, uint64_t seed)
     int64_t N = 0;
     for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
     if (N > L->V) return PSCO_E_FULL;
+    /* each compartment must hold its species' molecules */
+    {
+        int64_t room[PSCO_MAX_COMPARTMENTS] = {0}, need[PSCO_MAX_COMPARTMENTS] = {0};
+        for (int64_t v = 0; v < L->V; ++v) room[vcomp(L, v)]++;
+        for (int s = 0; s < L->nsp; ++s) need[L->sp[s].comp] += L->sp[s].n0;
+        for (int c = 0; c < L->ncomp; ++c)
+            if (need[c] > room[c]) return PSCO_E_FULL;
+    }
+    if (!reactions_fit_compartments(L)) return PSCO_E_UNSUPPORTED;
     L->seed = seed;
     int clamped = freeze_constants(L);
 
@@ -474,12 +546,17 @@ int psco_populate(psco_lattice *L, uint64_t seed)
         L->who[v] = -1;
     }
     qsort(kv, (size_t)L->V, sizeof(uint64_t), cmp_u64);
+    /* species in index order take the next voxels of their own compartment
+       in that order (with one compartment: the next voxels) */
+    int64_t cursor[PSCO_MAX_COMPARTMENTS] = {0};
     int64_t r = 0;
     for (int s = 0; s < L->nsp; ++s) {
+        const int32_t c = L->sp[s].comp;
         for (int64_t a = 0; a < L->sp[s].n0; ++a, ++r) {
             int64_t m = mol_new(L);
             if (m < 0) { free(kv); return PSCO_E_NOMEM; }
-            int32_t v = (int32_t)(kv[r] & 0xFFFFFFFFu);
+            while (vcomp(L, (int64_t)(kv[cursor[c]] & 0xFFFFFFFFu)) != c) cursor[c]++;
+            int32_t v = (int32_t)(kv[cursor[c]++] & 0xFFFFFFFFu);
             L->mol[m].v = v;
             L->mol[m].id = (uint32_t)r;
             L->mol[m].img[0] = L->mol[m].img[1] = L->mol[m].img[2] = 0;
@@ -525,28 +602,30 @@ static int32_t pick_first_order(const ospec *S, uint32_t u3)
     return S->fo[S->n_fo - 1];
 }
 
-/* vacant in-box neighbours of molecule m in direction order; returns count */
-static int vacant_neighbors(const psco_lattice *L, int32_t v, int64_t tv[12], int16_t tw[12][3])
+/* vacant in-box neighbours of voxel v that lie in compartment c, in
+   direction order; returns their count */
+static int vacant_neighbors(const psco_lattice *L, int32_t v, int32_t c, int64_t tv[12], int16_t tw[12][3])
 {
     int32_t ijk[3], o[3], w[3];
-    int c = 0;
+    int n = 0;
     decode(L, v, ijk);
     for (int d = 0; d < 12; ++d) {
         if (!psco_neighbor(L, ijk[0], ijk[1], ijk[2], d, o, w)) continue;
         int64_t t = encode(L, o);
-        if (L->occ[t] != 0) continue;
-        tv[c] = t;
-        tw[c][0] = (int16_t)w[0]; tw[c][1] = (int16_t)w[1]; tw[c][2] = (int16_t)w[2];
-        ++c;
+        if (L->occ[t] != 0 || vcomp(L, t) != c) continue;
+        tv[n] = t;
+        tw[n][0] = (int16_t)w[0]; tw[n][1] = (int16_t)w[1]; tw[n][2] = (int16_t)w[2];
+        ++n;
     }
-    return c;
+    return n;
 }
 
 /* Decide what molecule m of species s does in event g, looking at the grid as
    it is now.  Sec. 2.4.1 (first-order test, once per diffusion event; a
    molecule that fires does not hop -- reading), Sec. 2.3 (hop to a random
-   neighbour if vacant), Sec. 2.4.2 (collision with a registered partner
-   reacts with probability p_AB). */
+   neighbour if it is vacant and in the molecule's own compartment), Sec.
+   2.4.2 (collision with a registered partner reacts with probability p_AB,
+   whatever the partner's compartment -- reading). */
 static void decide(psco_lattice *L, int32_t s, uint32_t g, int64_t m, intent *it)
 {
     const ospec *S = &L->sp[s];
@@ -563,7 +642,7 @@ static void decide(psco_lattice *L, int32_t s, uint32_t g, int64_t m, intent *it
         it->rx = r;
         if (L->rx[r].np < 2) { it->kind = K_FIRE_INPLACE; return; }
         int64_t tv[12]; int16_t tw[12][3];
-        int c = vacant_neighbors(L, M->v, tv, tw);
+        int c = vacant_neighbors(L, M->v, L->sp[L->rx[r].p[1]].comp, tv, tw);
         if (c == 0) return;                           /* no room: reaction fails */
         int j = (int)(((uint64_t)u[0] * (uint64_t)c) >> 32);
         it->kind = K_FIRE2;
@@ -581,7 +660,10 @@ static void decide(psco_lattice *L, int32_t s, uint32_t g, int64_t m, intent *it
     uint16_t occ = L->occ[t];
     it->t = t;
     it->wrap[0] = (int16_t)w[0]; it->wrap[1] = (int16_t)w[1]; it->wrap[2] = (int16_t)w[2];
-    if (occ == 0) { it->kind = K_HOP; return; }
+    if (occ == 0) {
+        if (vcomp(L, t) == S->comp) it->kind = K_HOP;   /* else: another compartment */
+        return;
+    }
     int32_t partner = (int32_t)occ - 1;
     if (partner >= L->nsp) return;
     int32_t r = L->pair[s][partner];
@@ -625,9 +707,11 @@ static int place_birth(psco_lattice *L, const birth *B, uint32_t id)
 
 /* Carry out a decided action.  Products of a second-order reaction: the first
    takes the partner's voxel and identity, the second the mover's (reading of
-   Sec. 2.4.2, which does not say where products go).  First-order: the first
-   product keeps the reactant's voxel and identity, the second goes to the
-   chosen vacant neighbour (Sec. 2.4.1). */
+   Sec. 2.4.2, which does not say where products go); when that would put a
+   product outside its compartment, the two trade places (each product always
+   lands in its own compartment, and takes the identity of the reactant whose
+   voxel it takes).  First-order: the first product keeps the reactant's voxel
+   and identity, the second goes to the chosen vacant neighbour (Sec. 2.4.1). */
 static int apply(psco_lattice *L, int32_t s, const intent *it, birth *out_birth, int *has_birth)
 {
     omol *M = &L->mol[it->m];
@@ -645,18 +729,27 @@ static int apply(psco_lattice *L, int32_t s, const intent *it, birth *out_birth,
         const orx *R = &L->rx[it->rx];
         int64_t pm = L->who[it->t];
         L->st.reactions2++;
+        int straight = R->np == 0 ||
+                       (L->sp[R->p[0]].comp == vcomp(L, it->t) &&
+                        (R->np < 2 || L->sp[R->p[1]].comp == vcomp(L, M->v)));
         if (R->np == 0) {
             L->occ[it->t] = 0; L->who[it->t] = -1; set_species(L, pm, -1);
             L->occ[M->v] = 0;  L->who[M->v] = -1;  set_species(L, it->m, -1);
-        } else if (R->np == 1) {
+        } else if (R->np == 1 && straight) {
             set_species(L, pm, R->p[0]);
             L->occ[it->t] = (uint16_t)(R->p[0] + 1);
             L->occ[M->v] = 0;  L->who[M->v] = -1;  set_species(L, it->m, -1);
+        } else if (R->np == 1) {
+            set_species(L, it->m, R->p[0]);
+            L->occ[M->v] = (uint16_t)(R->p[0] + 1);
+            L->occ[it->t] = 0; L->who[it->t] = -1; set_species(L, pm, -1);
         } else {
-            set_species(L, pm, R->p[0]);
-            L->occ[it->t] = (uint16_t)(R->p[0] + 1);
-            set_species(L, it->m, R->p[1]);
-            L->occ[M->v] = (uint16_t)(R->p[1] + 1);
+            int32_t at_t = straight ? R->p[0] : R->p[1];
+            int32_t at_m = straight ? R->p[1] : R->p[0];
+            set_species(L, pm, at_t);
+            L->occ[it->t] = (uint16_t)(at_t + 1);
+            set_species(L, it->m, at_m);
+            L->occ[M->v] = (uint16_t)(at_m + 1);
         }
         break;
     }
@@ -998,6 +1091,7 @@ int psco_place(psco_lattice *L, int32_t s, int32_t v, uint32_t *id_out)
     if (!L || s < 0 || s >= L->nsp || v < 0 || v >= L->V) return PSCO_E_ARG;
     if (!L->populated) return PSCO_E_ORDER;
     if (L->occ[v] != 0) return PSCO_E_FULL;
+    if (vcomp(L, v) != L->sp[s].comp) return PSCO_E_ARG;
     int64_t m = mol_new(L);
     if (m < 0) return PSCO_E_NOMEM;
     L->mol[m].v = v;
@@ -1022,6 +1116,7 @@ int psco_check(const psco_lattice *L)
             if (m >= L->nmol) return 2;
             if (L->mol[m].v != v) return 3;
             if (L->mol[m].species + 1 != L->occ[v]) return 4;
+            if (L->sp[L->mol[m].species].comp != vcomp(L, v)) return 6;
         }
     }
     for (int64_t m = 0; m < L->nmol; ++m) {

@@ -14,8 +14,10 @@
  *                 (figures only) the FCC lattice in the same coordinates, ABC
  *                 stacking (layer offsets chosen by k mod 3).
  *   Sec. 2.2      event scheduler: per-species diffusion events in time order.
+ *   Sec. 2        compartments: groups of voxels; every species lives in one.
  *   Sec. 2.3      diffusion: hop interval tau_d = 2 r_v^2 / (3 D); a molecule
- *                 moves to a randomly chosen neighbour only if it is vacant.
+ *                 moves to a randomly chosen neighbour only if it is vacant
+ *                 and in the molecule's compartment.
  *   Sec. 2.4.1    first-order reactions (modified Gillespie direct method).
  *   Sec. 2.4.2    second-order reactions, discrete Collins-Kimball acceptance
  *                 p_AB = k / (6 sqrt(2) (D_A + D_B) r_v) on collision.
@@ -64,6 +66,7 @@ extern "C" {
 
 #define PSCO_MAX_SPECIES    64
 #define PSCO_MAX_REACTIONS 256
+#define PSCO_MAX_COMPARTMENTS 16
 
 /* boundary flag bits: set = periodic, clear = reflective wall */
 #define PSCO_PERIODIC_I 1u
@@ -95,6 +98,12 @@ int  psco_add_species(psco_lattice *L, double D_m2_s, int64_t initial_count,
 int  psco_add_reaction(psco_lattice *L, const int32_t *reactants, int32_t n_reactants,
                        const int32_t *products, int32_t n_products, double k,
                        int32_t *reaction_out);
+/* compartments (Sec. 2; before populate): labels[v], v = i + ni (j + nj k),
+   in [0, n); a species lives in compartment 0 unless set.  A hop into a
+   voxel of another compartment fails (Sec. 2.3); collisions with partners
+   react across compartments; placement fills each compartment on its own. */
+int  psco_set_compartments(psco_lattice *L, const uint8_t *labels, int32_t n_compartments);
+int  psco_species_compartment(psco_lattice *L, int32_t species, int32_t compartment);
 int  psco_populate(psco_lattice *L, uint64_t seed);
 int  psco_run(psco_lattice *L, double t_end);
 int  psco_run_events(psco_lattice *L, int64_t n_events);
@@ -107,7 +116,7 @@ int  psco_grid(const psco_lattice *L, uint16_t *occ);
 int  psco_time(const psco_lattice *L, double *t);
 int  psco_event_index(const psco_lattice *L, uint32_t *g);
 int  psco_stats_get(const psco_lattice *L, psco_stats *s);
-int  psco_check(const psco_lattice *L);     /* 0 if grid and molecules agree */
+int  psco_check(const psco_lattice *L);     /* 0 if grid, molecules and compartments agree */
 /* test helper: after populate, put one molecule of `species` on vacant voxel v;
    it takes the next fresh id */
 int  psco_place(psco_lattice *L, int32_t species, int32_t v, uint32_t *id_out);

@@ -68,3 +68,43 @@ def mapk_like(L, seed, scale=1.0, uni_scale=1.0, bi_scale=1.0):
         L.add_reaction([sp[es]], [sp[e], sp[s]], uni_scale * logu(0.1, 100.0))
         L.add_reaction([sp[es]], [sp[e], sp[p]], uni_scale * logu(0.1, 100.0))
     return len(sp)
+
+
+def cell_labels(ni, nj, nk, radius, shell=1.5):
+    """Compartment labels of a round cell in the middle of the box: 0 outside,
+    1 a membrane shell, 2 the cytoplasm.  The shape is an ellipsoid in index
+    space with nominal spacings 2, 1.73, 1.63 voxel radii along i, j, k and the
+    given radius and shell thickness in the same units.  Returns uint8 labels,
+    flat in v = i + ni (j + nj k)."""
+    import numpy as np
+    k, j, i = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+    r = np.sqrt((2.0 * (i - (ni - 1) / 2.0)) ** 2 + (1.73 * (j - (nj - 1) / 2.0)) ** 2 +
+                (1.63 * (k - (nk - 1) / 2.0)) ** 2)
+    lab = np.zeros((nk, nj, ni), dtype=np.uint8)
+    lab[r < radius] = 1
+    lab[r < radius - shell] = 2
+    return lab.reshape(-1)
+
+
+def receptor_binding(L, labels, n_ligand, n_receptor, n_x=0, n_outside=0, kon=5e-19, koff=20.0, kx=5e-19):
+    """A ligand in the cytoplasm (compartment 2) and a receptor that diffuses in
+    the membrane (compartment 1): L + R -> LR (the complex in the membrane),
+    LR -> R + L (the ligand released into the cytoplasm), X + R -> R + L (a
+    cytoplasmic X turned into ligand by the receptor it meets: the products
+    trade places when the receptor is the one that moves), and a walker outside
+    the cell (compartment 0).  Returns the species indices (L, R, LR, X, O)."""
+    L.set_compartments(labels, 3)
+    lig = L.add_species(1e-12, n_ligand)
+    rec = L.add_species(0.1e-12, n_receptor)
+    lr = L.add_species(0.05e-12, 0)
+    x = L.add_species(2e-12, n_x)
+    out = L.add_species(1e-12, n_outside)
+    L.species_compartment(lig, 2)
+    L.species_compartment(rec, 1)
+    L.species_compartment(lr, 1)
+    L.species_compartment(x, 2)
+    L.species_compartment(out, 0)
+    L.add_reaction([lig, rec], [lr], kon)
+    L.add_reaction([lr], [rec, lig], koff)
+    L.add_reaction([x, rec], [rec, lig], kx)
+    return lig, rec, lr, x, out

@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--replicas", type=int, default=512, help="replicas of the serving workload")
     ap.add_argument("--serial-sample", type=int, default=16, help="replicas timed one at a time")
+    ap.add_argument("--compartments", default="none", choices=["none", "cell"],
+                    help="cell: the same lattice holding a round cell (outside, membrane, cytoplasm) "
+                         "with the walkers in its cytoplasm")
     ap.add_argument("--rule", default="sync", choices=["sync", "subvolume"],
                     help="update rule: synchronous claims (the paper's hot path on the GPU), or the "
                          "sub-volume colouring rule (Sec. 2.5), for comparison")
@@ -206,12 +209,43 @@ def profiled_traffic(name):
         return None
 
 
-def make_lattice(psc, seed, device, stream, rule="sync"):
-    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=device, stream=stream)
-    L.add_species(D, N_MOL)
+_CELL = None
+
+
+def cell_labels():
+    """Compartments of the cell workload: an ellipsoid in index space (nominal
+    spacings 2, 1.73, 1.63 voxel radii along i, j, k) of radius 400 voxel
+    radii in the middle of the box; 0 outside, 1 a membrane shell 1.5 voxel
+    radii thick, 2 the cytoplasm (35 % of the voxels).  Built slab by slab."""
+    global _CELL
+    if _CELL is None:
+        ni, nj, nk = SHAPE
+        lab = np.zeros((nk, nj, ni), dtype=np.uint8)
+        j, i = np.meshgrid(np.arange(nj), np.arange(ni), indexing="ij")
+        rij = (2.0 * (i - (ni - 1) / 2.0)) ** 2 + (1.73 * (j - (nj - 1) / 2.0)) ** 2
+        for k in range(nk):
+            r = np.sqrt(rij + (1.63 * (k - (nk - 1) / 2.0)) ** 2)
+            sl = lab[k]
+            sl[r < 400.0] = 1
+            sl[r < 398.5] = 2
+        _CELL = lab.reshape(-1)
+    return _CELL
+
+
+def model(psc, L, args):
+    if args.compartments == "cell":
+        L.set_compartments(cell_labels(), 3)
+        L.add_species(D, N_MOL, compartment=2)
+    else:
+        L.add_species(D, N_MOL)
     L.set_options(resort_period=RESORT_PERIOD)
-    if rule == "subvolume":
+    if args.rule == "subvolume":
         L.set_options(subvolume=1)
+
+
+def make_lattice(psc, seed, device, stream, args):
+    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=device, stream=stream)
+    model(psc, L, args)
     L.populate(seed)
     return L
 
@@ -225,7 +259,7 @@ def gpu_arm(args, rank, world, local):
     ranks = Ranks(rank, world, "nccl", local)
     barrier = ranks.barrier
     stream = torch.cuda.Stream(device=local)
-    L = make_lattice(psc, replica_seed(rank), local, stream.cuda_stream, args.rule)
+    L = make_lattice(psc, replica_seed(rank), local, stream.cuda_stream, args)
 
     # warm-up
     for _ in range(args.warmup):
@@ -278,7 +312,7 @@ def gpu_arm(args, rank, world, local):
     tr = profiled_traffic("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
     traffic = None
     events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
-    if persistent and args.rule == "sync" and tr and tr.get("kernel_rev") == kernel_revision() and \
+    if persistent and args.rule == "sync" and args.compartments == "none" and tr and tr.get("kernel_rev") == kernel_revision() and \
             int(tr.get("events_per_launch", 0)) == round(events_per_launch):
         traffic = int(tr["dram_read_bytes"]) + int(tr["dram_write_bytes"])
     roofline = {
@@ -329,10 +363,7 @@ def e2e_run(psc, args, rank, local, torch, ranks):
     ranks.barrier()
     t0 = time.perf_counter()
     L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=local)
-    L.add_species(D, N_MOL)
-    L.set_options(resort_period=RESORT_PERIOD)
-    if args.rule == "subvolume":
-        L.set_options(subvolume=1)
+    model(psc, L, args)
     L.populate(replica_seed(rank))
     for _ in range(args.steps):
         L.run_events(EVENTS_PER_STEP)
@@ -454,17 +485,23 @@ def serving_arm(args, local):
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_lattice(seed):
+def oracle_lattice(seed, args):
+    """The same workload on the oracle, under the same update rule."""
     import oracle
-    L = oracle.Lattice(*SHAPE, RV, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
-    L.add_species(D, N_MOL)
+    rule = oracle.RULE_SUBVOL if args.rule == "subvolume" else oracle.RULE_SYNC
+    L = oracle.Lattice(*SHAPE, RV, oracle.PERIODIC_ALL, rule)
+    if args.compartments == "cell":
+        L.set_compartments(cell_labels(), 3)
+        L.add_species(D, N_MOL, compartment=2)
+    else:
+        L.add_species(D, N_MOL)
     L.populate(seed)
     return L
 
 
-def cpu_baseline(seconds):
+def cpu_baseline(seconds, args):
     t0 = time.perf_counter()
-    L = oracle_lattice(1)
+    L = oracle_lattice(1, args)
     t_pop = time.perf_counter() - t0
     L.run_events(1)                                    # calibrate
     t1 = time.perf_counter()
@@ -480,10 +517,16 @@ def cpu_baseline(seconds):
                       "single thread, %s" % (n, N_MOL, t_pop, cpu_model())}
 
 
+def workload_name(args):
+    return (WORKLOAD + ("; sub-volume update rule" if args.rule == "subvolume" else "") +
+            ("; in a round cell (outside, membrane, cytoplasm), the walkers in its cytoplasm"
+             if args.compartments == "cell" else ""))
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return None
-    L = oracle_lattice(1)
+    L = oracle_lattice(1, args)
     for _ in range(args.warmup):
         L.run_events(1)
     t0 = time.perf_counter()
@@ -496,8 +539,8 @@ def reference_arm(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": "1 hop interval (oracle)", "lattice": list(SHAPE),
-                   "molecules": N_MOL},
+        "config": {"workload": workload_name(args), "step": "1 hop interval (oracle)", "lattice": list(SHAPE),
+                   "molecules": N_MOL, "rule": args.rule, "compartments": args.compartments},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d + %d warm-up events of the 512^3 lattice, single thread, %s"
@@ -522,8 +565,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["elapsed_ms"] / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.rule == "sync" else WORKLOAD + "; sub-volume update rule",
-                   "rule": args.rule, "lattice": list(SHAPE), "molecules": N_MOL,
+        "config": {"workload": workload_name(args),
+                   "rule": args.rule, "compartments": args.compartments, "lattice": list(SHAPE), "molecules": N_MOL,
                    "events_per_step": EVENTS_PER_STEP, "resort_period": RESORT_PERIOD,
                    "replicas": world, "l2": "inputs larger than L2 (occupancy 268 MB + claim words 537 MB)",
                    "parallelism": "replicas (one independent lattice per GPU)"},
@@ -536,7 +579,7 @@ def main():
     if world == 1 and not args.no_serving:
         out["serving"] = serving_arm(args, local)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args)
     print(json.dumps(out))
 
 

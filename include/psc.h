@@ -89,6 +89,7 @@ extern "C" {
 
 #define PSC_MAX_SPECIES    32
 #define PSC_MAX_REACTIONS 128
+#define PSC_MAX_COMPARTMENTS 16
 
 typedef struct psc_lattice psc_lattice;
 
@@ -208,12 +209,42 @@ int psc_add_reaction(psc_lattice *L, const int32_t *reactants, int32_t n_reactan
                      const int32_t *products, int32_t n_products, double k,
                      int32_t *reaction_out);
 
+/* Compartments (Sec. 2: a cell is a set of compartments, each a group of
+   voxels).  labels: host buffer of V bytes, labels[i + ni (j + nj k)] = the
+   compartment of voxel (i, j, k), each below n_compartments (1 ..
+   PSC_MAX_COMPARTMENTS); the library copies it, the caller keeps ownership.
+   Every species lives in one compartment, 0 unless psc_species_compartment
+   says otherwise.  Effects (Sec. 2.3): a hop into a voxel of another
+   compartment fails like a hop into an occupied voxel; a collision with a
+   registered partner reacts whatever the partner's compartment; products of
+   a second-order reaction go to the two reactants' voxels, the first product
+   to the partner's and the second to the mover's unless that puts one outside
+   its compartment, in which case they trade places (each product takes the id
+   of the reactant whose voxel it takes); the second product of a first-order
+   reaction goes to a vacant neighbour in its own compartment; placement
+   deals each compartment's voxels to its own species.  Before psc_populate;
+   calling it again replaces the labels.  Errors: E_ARG (labels NULL, a label
+   >= n_compartments, n_compartments out of range, a species already set to a
+   compartment >= n_compartments), E_ORDER. */
+int psc_set_compartments(psc_lattice *L, const uint8_t *labels, int32_t n_compartments);
+
+/* The compartment species lives in (below the n_compartments of the last
+   psc_set_compartments, 0 without one).  Before psc_populate.  Errors: E_ARG,
+   E_ORDER. */
+int psc_species_compartment(psc_lattice *L, int32_t species, int32_t compartment);
+
 /* Freeze the model, allocate device state and place the molecules uniformly
    at random without replacement (Sec. 3.4 "distributed homogeneously"):
    every voxel gets the key Philox(seed; v, 0, 1, 0) word 0, voxels sorted by
    (key, v) are dealt to the species in index order, ids 0, 1, ... in that
-   order.  Synchronous.  Returns PSC_W_PCLAMP if some p_AB > 1 was clamped.
-   Errors: E_ARG, E_ORDER (twice), E_FULL, E_NOMEM, E_CUDA. */
+   order (with compartments: each species takes the next voxels of its own
+   compartment in that order).  Synchronous.  Returns PSC_W_PCLAMP if some
+   p_AB > 1 was clamped.  Errors: E_ARG, E_ORDER (twice), E_FULL (more
+   molecules than voxels, in the lattice or in one compartment), E_UNSUPPORTED
+   (a reaction whose products cannot all land in their compartments: a
+   first-order product that stays must share the reactant's compartment, the
+   products of A + B must be one in each reactant's compartment, a single
+   one in either), E_NOMEM, E_CUDA. */
 int psc_populate(psc_lattice *L, uint64_t seed);
 
 /* Queue every event with time <= t_end (Sec. 2.2); the lattice clock becomes

@@ -154,6 +154,8 @@ class Lattice:
     def set_compartments(self, labels, n):
         """labels: uint8 per voxel, flat (v = i + ni (j + nj k)) or shaped (nk, nj, ni)."""
         lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+        if lab.size != self.shape[0] * self.shape[1] * self.shape[2]:
+            raise ValueError("labels: one byte per voxel")
         _check("psco_set_compartments", lib().psco_set_compartments(self._h, _ptr(lab), int(n)))
 
     def species_compartment(self, species, c):

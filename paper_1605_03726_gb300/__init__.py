@@ -19,6 +19,7 @@ W_PCLAMP = 1
 PERIODIC_I, PERIODIC_J, PERIODIC_K, PERIODIC_ALL = 1, 2, 4, 7
 FCC = 8                       # lattice flag: FCC (ABC stacking) instead of HCP
 MAX_SPECIES = 32
+MAX_COMPARTMENTS = 16
 
 _lib = None
 
@@ -102,6 +103,8 @@ def lib():
             "psc_add_species": (ctypes.c_int, [P, dbl, i64, ctypes.POINTER(i32)]),
             "psc_add_reaction": (ctypes.c_int, [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32, dbl,
                                                 ctypes.POINTER(i32)]),
+            "psc_set_compartments": (ctypes.c_int, [P, P, i32]),
+            "psc_species_compartment": (ctypes.c_int, [P, i32, i32]),
             "psc_populate": (ctypes.c_int, [P, u64]),
             "psc_run": (ctypes.c_int, [P, dbl]),
             "psc_run_events": (ctypes.c_int, [P, i64]),
@@ -147,7 +150,8 @@ def lib():
     return _lib
 
 
-EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_populate", "psc_run",
+EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_set_compartments",
+            "psc_species_compartment", "psc_populate", "psc_run",
             "psc_run_events", "psc_synchronize", "psc_counts", "psc_coords", "psc_unwrapped", "psc_grid",
             "psc_time", "psc_event_index", "psc_stats_get", "psc_set_options", "psc_kernel_times_get",
             "psc_autotune", "psc_batch_autotune", "psc_tau", "psc_p_ab",
@@ -230,11 +234,23 @@ class Lattice:
     def __exit__(self, *exc):
         self.close()
 
-    def add_species(self, D, count):
+    def add_species(self, D, count, compartment=None):
         s = ctypes.c_int32()
         _check("psc_add_species", lib().psc_add_species(self._h, float(D), int(count), ctypes.byref(s)))
         self.n_species += 1
+        if compartment is not None:
+            self.species_compartment(s.value, compartment)
         return s.value
+
+    def set_compartments(self, labels, n):
+        """labels: uint8 per voxel, flat (v = i + ni (j + nj k)) or shaped (nk, nj, ni)."""
+        lab = np.ascontiguousarray(np.asarray(labels, dtype=np.uint8).reshape(-1))
+        if lab.size != self.shape[0] * self.shape[1] * self.shape[2]:
+            raise ValueError("labels: one byte per voxel")
+        _check("psc_set_compartments", lib().psc_set_compartments(self._h, _ptr(lab), int(n)))
+
+    def species_compartment(self, species, c):
+        _check("psc_species_compartment", lib().psc_species_compartment(self._h, int(species), int(c)))
 
     def add_reaction(self, reactants, products, k):
         r = (ctypes.c_int32 * max(1, len(reactants)))(*reactants)

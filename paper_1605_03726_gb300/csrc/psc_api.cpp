@@ -103,7 +103,7 @@ EventArgs event_args(const psc_lattice* L, int s)
     a.geo = L->geo;
     a.geo.slot_map = (uint32_t)(L->opt.slot_map - 1);
     a.occ = L->occ;
-    a.bits = L->bits;
+    a.bits = L->bits + (size_t)L->sp[s].comp * L->mirror_n;
     a.ct.direct = L->claim;
     if (L->tables[0]) {
         const int cur = (int)(L->g & 1u), other = cur ^ 1;
@@ -179,7 +179,7 @@ ReconcileArgs reconcile_args(const psc_lattice* L, int x)
     ReconcileArgs r{};
     r.geo = L->geo;
     r.occ = L->occ;
-    r.bits = L->bits;
+    r.bits = L->bits + (size_t)L->sp[x].comp * L->mirror_n;
     r.x = x;
     r.list = L->model_h.lists[x];
     r.tmp = L->tmp;
@@ -601,6 +601,29 @@ int psc_add_reaction(psc_lattice* L, const int32_t* re, int32_t nr, const int32_
     return PSC_OK;
 }
 
+int psc_set_compartments(psc_lattice* L, const uint8_t* labels, int32_t n)
+{
+    if (!L || !labels) return PSC_E_ARG;
+    if (L->populated) return PSC_E_ORDER;
+    if (n < 1 || n > kMaxCompartments) return PSC_E_ARG;
+    for (int64_t v = 0; v < L->V; ++v)
+        if (labels[v] >= n) return PSC_E_ARG;
+    for (int s = 0; s < L->nsp; ++s)
+        if (L->sp[s].comp >= n) return PSC_E_ARG;
+    L->labels.assign(labels, labels + L->V);
+    L->ncomp = n;
+    return PSC_OK;
+}
+
+int psc_species_compartment(psc_lattice* L, int32_t s, int32_t c)
+{
+    if (!L || s < 0 || s >= L->nsp) return PSC_E_ARG;
+    if (L->populated) return PSC_E_ORDER;
+    if (c < 0 || c >= L->ncomp) return PSC_E_ARG;
+    L->sp[s].comp = c;
+    return PSC_OK;
+}
+
 double psc_tau(const psc_lattice* L, int32_t s)
 {
     if (!L || s < 0 || s >= L->nsp || !(L->sp[s].D > 0.0)) return 0.0;
@@ -621,6 +644,40 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     int64_t N = 0;
     for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
     if (N > L->V) return PSC_E_FULL;
+    // compartments: room in each, products that can land in theirs, and the
+    // first sorted voxel of each species (species of one compartment take its
+    // voxels one after another, in species order)
+    const bool comps = !L->labels.empty();
+    int64_t start[kMaxSpecies] = {};
+    {
+        int64_t room[kMaxCompartments] = {}, base[kMaxCompartments + 1] = {}, used[kMaxCompartments] = {};
+        if (comps) {
+            for (int64_t v = 0; v < L->V; ++v) room[L->labels[v]]++;
+        } else {
+            room[0] = L->V;
+        }
+        for (int c = 0; c < L->ncomp; ++c) base[c + 1] = base[c] + room[c];
+        for (int s = 0; s < L->nsp; ++s) {
+            const int c = L->sp[s].comp;
+            start[s] = base[c] + used[c];
+            used[c] += L->sp[s].n0;
+            if (used[c] > room[c]) return PSC_E_FULL;
+        }
+        for (int r = 0; r < L->nrx; ++r) {
+            const Reaction& R = L->rx[r];
+            const int ca = L->sp[R.r[0]].comp;
+            if (R.nr == 1) {
+                if (R.np >= 1 && L->sp[R.p[0]].comp != ca) return PSC_E_UNSUPPORTED;
+                continue;
+            }
+            const int cb = L->sp[R.r[1]].comp;
+            if (R.np == 1 && L->sp[R.p[0]].comp != ca && L->sp[R.p[0]].comp != cb) return PSC_E_UNSUPPORTED;
+            if (R.np == 2) {
+                const int c0 = L->sp[R.p[0]].comp, c1 = L->sp[R.p[1]].comp;
+                if (!((c0 == ca && c1 == cb) || (c0 == cb && c1 == ca))) return PSC_E_UNSUPPORTED;
+            }
+        }
+    }
     DevGuard dg(L->device);
     L->seed = seed;
 
@@ -706,8 +763,10 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     // ---- device memory ----
     const size_t V = (size_t)L->V;
     const size_t nwords = (size_t)mirror_words(L->ni, L->nj, L->nk);
+    const int nmirror = comps ? L->ncomp : 1;
+    L->mirror_n = nwords;
     L->occ = (uint16_t*)dev_alloc(L, V * sizeof(uint16_t));
-    L->bits = (uint32_t*)dev_alloc(L, nwords * sizeof(uint32_t));
+    L->bits = (uint32_t*)dev_alloc(L, nwords * nmirror * sizeof(uint32_t));
     L->sc = (Scalars*)dev_alloc(L, sizeof(Scalars));
     L->model_d = (ModelDev*)dev_alloc(L, sizeof(ModelDev));
     L->barrier = (BarrierState*)dev_alloc(L, sizeof(BarrierState));
@@ -746,6 +805,8 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         }
     }
     for (int s = 0; s < L->nsp; ++s) {
+        M.comp[s] = (uint8_t)(comps ? L->sp[s].comp : 0);
+        M.mirror[s] = L->bits + (size_t)M.comp[s] * nwords;
         SpeciesList& l = M.lists[s];
         l.cap = L->cap[s];
         l.vox = (int32_t*)dev_alloc(L, (size_t)l.cap * 4);
@@ -797,8 +858,20 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     sh.next_id = (uint32_t)N;
     if ((rc = cuda_fail(L, cudaMemcpyAsync(L->sc, &sh, sizeof(sh), cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->occ, 0, V * sizeof(uint16_t), st)))) return rc;
-    if ((rc = cuda_fail(L, cudaMemsetAsync(L->bits, 0, nwords * sizeof(uint32_t), st)))) return rc;
     const int fill_blocks = L->sm_count * 8;
+    uint8_t* labels_d = nullptr;
+    if (comps) {
+        // the labels are needed on the device only while placing
+        labels_d = (uint8_t*)dev_alloc(L, V);
+        if (!labels_d) return PSC_E_NOMEM;
+        if ((rc = cuda_fail(L, cudaMemcpyAsync(labels_d, L->labels.data(), V, cudaMemcpyHostToDevice, st))))
+            return rc;
+        L->h2d += V;
+        launch_mirror_walls(L->bits, nwords, nmirror, labels_d, L->geo, fill_blocks, st);
+        L->launches += 1;
+    } else if ((rc = cuda_fail(L, cudaMemsetAsync(L->bits, 0, nwords * sizeof(uint32_t), st)))) {
+        return rc;
+    }
     if (L->claim) launch_fill_u32(L->claim, kNoClaim, V, fill_blocks, st);
     for (int t = 0; t < 2; ++t)
         if (L->tables[t]) launch_fill_u64(L->tables[t], kEmptySlot, (size_t)1 << hb_max, fill_blocks, st);
@@ -814,14 +887,25 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         launch_populate_keys(keys, vals, (uint32_t)V, (uint32_t)seed, (uint32_t)(seed >> 32), fill_blocks, st);
         if (radix_sort_pairs(keys, vals, nullptr, L->V, L->V, 32, ss, st, &L->launches) != 0)
             return cuda_fail(L, cudaErrorUnknown);
+        if (comps) {
+            // stable pass on the compartment: (compartment, key, voxel) order
+            launch_label_keys(vals, labels_d, keys, L->V, fill_blocks, st);
+            if (radix_sort_pairs(keys, vals, nullptr, L->V, L->V, 8, ss, st, &L->launches) != 0)
+                return cuda_fail(L, cudaErrorUnknown);
+            L->launches += 1;
+        }
         int64_t off[kMaxSpecies + 1];
         off[0] = 0;
         for (int s = 0; s < L->nsp; ++s) off[s + 1] = off[s] + L->sp[s].n0;
-        launch_populate_scatter(vals, N, off, L->nsp, L->occ, L->bits, L->geo, L->model_d, fill_blocks, st);
+        launch_populate_scatter(vals, N, off, start, L->nsp, L->occ, L->geo, L->model_d, fill_blocks, st);
         if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
         dev_free_one(L, keys);
         dev_free_one(L, vals);
         dev_free_one(L, scratch);
+    }
+    if (labels_d) {
+        if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
+        dev_free_one(L, labels_d);
     }
     if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
     L->g = 0;
@@ -1065,7 +1149,8 @@ int psc_grid(psc_lattice* L, uint16_t* occ)
     uint16_t* tmp = (uint16_t*)dev_alloc(L, (size_t)L->V * 2);
     if (!tmp) return PSC_E_NOMEM;
     const int blocks = L->sm_count * 8;
-    launch_materialize(tmp, L->occ, L->bits, L->geo, L->V, blocks, L->stream);
+    launch_materialize(tmp, L->occ, L->bits, L->mirror_n, L->labels.empty() ? 1 : L->ncomp, L->geo, L->V, blocks,
+                       L->stream);
     for (int s = 0; s < L->nsp; ++s)
         if (!L->live[s])
             launch_scatter_codes(tmp, L->model_h.lists[s], &L->sc->counts[s], (uint16_t)(s + 1), blocks,
@@ -1191,7 +1276,8 @@ int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
 int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
 {
     if (!L || !bytes) return PSC_E_ARG;
-    int64_t b = L->V * 2 + (int64_t)mirror_words(L->ni, L->nj, L->nk) * 4 + (int64_t)sizeof(Scalars) +
+    const int64_t mirrors = L->labels.empty() ? 1 : L->ncomp;
+    int64_t b = L->V * 2 + (int64_t)mirror_words(L->ni, L->nj, L->nk) * 4 * mirrors + (int64_t)sizeof(Scalars) +
                 (int64_t)sizeof(ModelDev);
     if (L->claim) b += L->V * 4;
     b += 2 * L->table_slots * 8;

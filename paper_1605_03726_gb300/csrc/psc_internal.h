@@ -13,6 +13,7 @@ namespace psc {
 constexpr int kMaxSpecies = 32;
 constexpr int kMaxReactions = 128;
 constexpr int kMaxFirstOrder = 8;          // first-order reactions per species
+constexpr int kMaxCompartments = 16;
 constexpr uint32_t kNoClaim = 0xFFFFFFFFu;  // claim word of an unclaimed voxel
 constexpr uint16_t kBlocked = 0xFFFFu;      // occupancy code reserved for walls
 constexpr uint32_t kTagEvent = 0u;          // Philox counter word 2 domain tags
@@ -86,6 +87,11 @@ struct ModelDev {
     int32_t fo_rx[kMaxSpecies][kMaxFirstOrder];
     uint64_t fo_cum[kMaxSpecies][kMaxFirstOrder];
     SpeciesList lists[kMaxSpecies];
+    // Compartments (Sec. 2): one vacancy mirror per compartment, in which the
+    // voxels of every other compartment are set for good, so a species tests
+    // vacancy-and-own-compartment with one bit of its own mirror
+    uint32_t* mirror[kMaxSpecies];           // the mirror of the species' compartment
+    uint8_t comp[kMaxSpecies];               // the species' compartment
 };
 
 enum StatIndex {
@@ -248,8 +254,16 @@ constexpr int kTileBlocksPerSM = 2;
 void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st);
 void launch_tile_gather(const TileArgs& A, cudaStream_t st);
-void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
-                        int64_t V, int blocks, cudaStream_t st);
+// mirror c of n: bit v set where labels[v] != c (walls), the rest clear
+void launch_mirror_walls(uint32_t* bits0, uint64_t words, int n, const uint8_t* labels, const Geometry& geo,
+                         int blocks, cudaStream_t st);
+// keys[r] = labels[vals[r]]: the compartment of each sorted voxel
+void launch_label_keys(const uint32_t* vals, const uint8_t* labels, uint32_t* keys, int64_t n, int blocks,
+                       cudaStream_t st);
+// codes where a voxel is occupied (its bit set in all n_mirrors mirrors of
+// `words` words each, starting at bits0), zero elsewhere
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits0, uint64_t words,
+                        int n_mirrors, const Geometry& geo, int64_t V, int blocks, cudaStream_t st);
 void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
                           int blocks, cudaStream_t st);
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
@@ -258,8 +272,11 @@ void launch_births(const EventArgs& a, cudaStream_t st);
 void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
 void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
                           int blocks, cudaStream_t st);
+// molecule r (ids in species order, species s owning [offsets[s],
+// offsets[s+1])) takes sorted_vox[starts[s] + r - offsets[s]]; its bit goes
+// to the mirror of its species' compartment
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, uint32_t* bits, const Geometry& geo,
+                             const int64_t* starts, int n_species, uint16_t* occ, const Geometry& geo,
                              const ModelDev* model, int blocks, cudaStream_t st);
 void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st);

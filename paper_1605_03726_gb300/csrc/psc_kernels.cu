@@ -385,16 +385,18 @@ __device__ __forceinline__ void claim_body(const EventArgs& a, uint32_t g, int b
                 const int r = pick_first_order(M, a.s, u[3]);
                 if (M->rx[r].np == 2) {
                     // second product: uniform pick among neighbours vacant now
+                    // in its compartment (clear in its compartment's mirror)
+                    const uint32_t* pb = M->mirror[M->rx[r].p1];
                     int c = 0;
                     for (int d = 0; d < 12; ++d) {
                         Nb nb;
-                        if (neighbor(a.geo, i, j, k, d, nb) && !occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) ++c;
+                        if (neighbor(a.geo, i, j, k, d, nb) && !occupied(pb, bitpos(a.geo, nb.i, nb.j, nb.k))) ++c;
                     }
                     if (c > 0) {
                         int want = (int)__umulhi(u[0], (uint32_t)c);
                         for (int d = 0; d < 12; ++d) {
                             Nb nb;
-                            if (neighbor(a.geo, i, j, k, d, nb) && !occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) {
+                            if (neighbor(a.geo, i, j, k, d, nb) && !occupied(pb, bitpos(a.geo, nb.i, nb.j, nb.k))) {
                                 if (want == 0) { claim<HASH>(a, nb, id); break; }
                                 --want;
                             }
@@ -472,14 +474,15 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                 if (R.np == 2) {
                     // the neighbour this molecule claimed, if it won it; only
                     // its winner changes the bit of a claimed voxel
+                    uint32_t* pb = M->mirror[R.p1];
                     for (int d = 0; d < 12; ++d) {
                         Nb nb;
                         if (!neighbor(a.geo, i, j, k, d, nb)) continue;
                         const BitPos bt = bitpos(a.geo, nb.i, nb.j, nb.k);
-                        if (occupied(a.bits, bt) || !won<HASH>(a, nb, id)) continue;
+                        if (occupied(pb, bt) || !won<HASH>(a, nb, id)) continue;
                         a.occ[v] = (uint16_t)(R.p0 + 1);
                         a.occ[nb.t] = (uint16_t)(R.p1 + 1);
-                        bit_set(a.bits, bt);
+                        bit_set(pb, bt);
                         const int slot = atomicAdd(&a.sc->births, 1);
                         if (slot < a.births_cap) {
                             Birth b;
@@ -521,21 +524,33 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
             if (nb.wrap) a.list.img[idx] = img_add(a.list.img[idx], nb.wrap);
             ++n_hop;
         } else {
-            // accepted collision with partner o - 1 (Sec. 2.4.2): first
-            // product on the partner's voxel, second on the mover's
-            const uint16_t o = a.occ[nb.t];
-            const ReactionDev R = a.model->rx[a.model->pair[a.s][o - 1]];
-            if (R.np >= 1) {
-                a.occ[nb.t] = (uint16_t)(R.p0 + 1);
-            } else {
+            // accepted collision with partner y = o - 1 (Sec. 2.4.2): first
+            // product on the partner's voxel, second on the mover's, unless
+            // that puts a product outside its compartment (then they trade
+            // places).  The partner's voxel is in y's compartment, its bit in
+            // y's mirror.
+            const ModelDev* M = a.model;
+            const int y = (int)a.occ[nb.t] - 1;
+            const ReactionDev R = M->rx[M->pair[a.s][y]];
+            uint32_t* tb = M->mirror[y];
+            const bool straight = R.np == 0 ||
+                                  (M->comp[R.p0] == M->comp[y] && (R.np < 2 || M->comp[R.p1] == M->comp[a.s]));
+            if (R.np == 0) {
                 a.occ[nb.t] = 0;
-                bit_clear(a.bits, bt);
-            }
-            if (R.np == 2) {
-                a.occ[v] = (uint16_t)(R.p1 + 1);
-            } else {
+                bit_clear(tb, bt);
                 a.occ[v] = 0;
                 bit_clear(a.bits, bv);
+            } else if (R.np == 1 && straight) {
+                a.occ[nb.t] = (uint16_t)(R.p0 + 1);
+                a.occ[v] = 0;
+                bit_clear(a.bits, bv);
+            } else if (R.np == 1) {
+                a.occ[v] = (uint16_t)(R.p0 + 1);
+                a.occ[nb.t] = 0;
+                bit_clear(tb, bt);
+            } else {
+                a.occ[nb.t] = (uint16_t)((straight ? R.p0 : R.p1) + 1);
+                a.occ[v] = (uint16_t)((straight ? R.p1 : R.p0) + 1);
             }
             ++n_r2;
         }
@@ -1054,21 +1069,69 @@ void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStre
 }
 
 // exact species grid for read-out: the codes of species with reactions where
-// the mirror says occupied, zero elsewhere; species without reactions are
-// written afterwards from their lists (they do not keep codes while moving)
-__global__ void k_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, Geometry G, int64_t V)
+// the mirrors say occupied, zero elsewhere; species without reactions are
+// written afterwards from their lists (they do not keep codes while moving).
+// A voxel is occupied when its bit is set in every compartment's mirror (in
+// all but its own compartment's it is a wall).
+__global__ void k_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits0, uint64_t words,
+                              int n_mirrors, Geometry G, int64_t V)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t i, j, k;
         decode(G, (uint32_t)v, i, j, k);
-        out[v] = occupied(bits, bitpos(G, i, j, k)) ? occ[v] : (uint16_t)0;
+        const BitPos b = bitpos(G, i, j, k);
+        bool full = true;
+        for (int c = 0; c < n_mirrors; ++c) full = full && occupied(bits0 + (uint64_t)c * words, b);
+        out[v] = full ? occ[v] : (uint16_t)0;
     }
 }
 
-void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits, const Geometry& geo,
-                        int64_t V, int blocks, cudaStream_t st)
+void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits0, uint64_t words,
+                        int n_mirrors, const Geometry& geo, int64_t V, int blocks, cudaStream_t st)
 {
-    k_materialize<<<blocks, 256, 0, st>>>(out, occ, bits, geo, V);
+    k_materialize<<<blocks, 256, 0, st>>>(out, occ, bits0, words, n_mirrors, geo, V);
+}
+
+// walls: one thread per mirror word builds that word of every mirror from
+// the labels of its 4 x 4 x 2 brick (voxels outside the lattice stay clear)
+__global__ void k_mirror_walls(uint32_t* bits0, uint64_t words, int n, const uint8_t* labels, Geometry G)
+{
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t bi = (uint32_t)(w % G.nbi);
+        const uint32_t bj = (uint32_t)((w / G.nbi) % G.nbj);
+        const uint32_t bk = (uint32_t)(w / ((uint64_t)G.nbi * G.nbj));
+        uint32_t m[kMaxCompartments];
+        for (int c = 0; c < n; ++c) m[c] = 0u;
+        for (uint32_t b = 0; b < 32; ++b) {
+            const int32_t i = (int32_t)(bi * 4 + (b & 3u));
+            const int32_t j = (int32_t)(bj * 4 + ((b >> 2) & 3u));
+            const int32_t k = (int32_t)(bk * 2 + (b >> 4));
+            if (i >= G.ni || j >= G.nj || k >= G.nk) continue;
+            const int lab = labels[(uint64_t)i + (uint64_t)G.ni * ((uint64_t)j + (uint64_t)G.nj * (uint64_t)k)];
+            for (int c = 0; c < n; ++c)
+                if (c != lab) m[c] |= 1u << b;
+        }
+        for (int c = 0; c < n; ++c) bits0[(uint64_t)c * words + w] = m[c];
+    }
+}
+
+void launch_mirror_walls(uint32_t* bits0, uint64_t words, int n, const uint8_t* labels, const Geometry& geo,
+                         int blocks, cudaStream_t st)
+{
+    k_mirror_walls<<<blocks, 256, 0, st>>>(bits0, words, n, labels, geo);
+}
+
+__global__ void k_label_keys(const uint32_t* vals, const uint8_t* labels, uint32_t* keys, int64_t n)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        keys[r] = labels[vals[r]];
+}
+
+void launch_label_keys(const uint32_t* vals, const uint8_t* labels, uint32_t* keys, int64_t n, int blocks,
+                       cudaStream_t st)
+{
+    k_label_keys<<<blocks, 256, 0, st>>>(vals, labels, keys, n);
 }
 
 __global__ void k_scatter_codes(uint16_t* out, const SpeciesList L, const int32_t* count, uint16_t code)
@@ -1105,20 +1168,21 @@ struct Offsets {
     int64_t off[kMaxSpecies + 1];
 };
 
-// rank r of the sorted voxels goes to the species whose range holds r
-__global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, Offsets o, int n_species,
-                                   uint16_t* occ, uint32_t* bits, Geometry G, const ModelDev* model)
+// molecule r (id r) belongs to the species whose id range holds r and takes
+// that species' next voxel of the sorted order
+__global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, Offsets o, Offsets start,
+                                   int n_species, uint16_t* occ, Geometry G, const ModelDev* model)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_total;
          r += (int64_t)gridDim.x * blockDim.x) {
         int s = 0;
         while (s + 1 < n_species && r >= o.off[s + 1]) ++s;
-        const uint32_t v = sorted_vox[r];
         const int64_t a = r - o.off[s];
+        const uint32_t v = sorted_vox[start.off[s] + a];
         occ[v] = (uint16_t)(s + 1);
         int32_t i, j, k;
         decode(G, v, i, j, k);
-        bit_set(bits, bitpos(G, i, j, k));
+        bit_set(model->mirror[s], bitpos(G, i, j, k));
         const SpeciesList L = model->lists[s];
         L.vox[a] = (int32_t)v;
         L.ids[a] = (uint32_t)r;
@@ -1127,12 +1191,15 @@ __global__ void k_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, 
 }
 
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
-                             int n_species, uint16_t* occ, uint32_t* bits, const Geometry& geo,
+                             const int64_t* starts, int n_species, uint16_t* occ, const Geometry& geo,
                              const ModelDev* model, int blocks, cudaStream_t st)
 {
-    Offsets o;
-    for (int s = 0; s <= kMaxSpecies; ++s) o.off[s] = s <= n_species ? offsets[s] : offsets[n_species];
-    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, n_species, occ, bits, geo, model);
+    Offsets o, b;
+    for (int s = 0; s <= kMaxSpecies; ++s) {
+        o.off[s] = s <= n_species ? offsets[s] : offsets[n_species];
+        b.off[s] = s < n_species ? starts[s] : 0;
+    }
+    k_populate_scatter<<<blocks, 256, 0, st>>>(sorted_vox, n_total, o, b, n_species, occ, geo, model);
 }
 
 // Morton (Z-order) key of the voxel of each list entry (compact code)

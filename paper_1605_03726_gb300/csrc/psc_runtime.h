@@ -20,6 +20,7 @@ struct Species {
     uint64_t done = 0;
     int n_fo = 0;
     int fo[kMaxFirstOrder] = {};
+    int comp = 0;                      // compartment (Sec. 2)
 };
 
 struct Reaction {
@@ -59,7 +60,10 @@ struct psc_lattice {
     ModelDev model_h{};
     ModelDev* model_d = nullptr;
     uint16_t* occ = nullptr;
-    uint32_t* bits = nullptr;          // vacancy mirror, one bit per voxel
+    uint32_t* bits = nullptr;          // vacancy mirrors, one bit per voxel, one mirror per compartment
+    uint64_t mirror_n = 0;             // words of one mirror
+    int32_t ncomp = 1;                 // compartments (Sec. 2)
+    std::vector<uint8_t> labels;       // compartment of every voxel (empty: all 0)
     uint32_t* claim = nullptr;         // per-voxel claim words (small lattices)
     uint64_t* tables[2] = {nullptr, nullptr};   // claim hash tables (large lattices)
     uint32_t table_used[2] = {0, 0};   // slots written by the event that used it

@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--compartments", default="none", choices=["none", "cell"],
                     help="cell: the same lattice holding a round cell (outside, membrane, cytoplasm) "
                          "with the walkers in its cytoplasm")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "list"],
+                    help="stretch kernel: the library's choice, the tile kernel, or the molecule-list kernel")
     ap.add_argument("--rule", default="sync", choices=["sync", "subvolume"],
                     help="update rule: synchronous claims (the paper's hot path on the GPU), or the "
                          "sub-volume colouring rule (Sec. 2.5), for comparison")
@@ -239,6 +241,8 @@ def model(psc, L, args):
     else:
         L.add_species(D, N_MOL)
     L.set_options(resort_period=RESORT_PERIOD)
+    if args.kernel != "auto":
+        L.set_options(tiles=1 if args.kernel == "tile" else -1)
     if args.rule == "subvolume":
         L.set_options(subvolume=1)
 
@@ -302,7 +306,9 @@ def gpu_arm(args, rank, world, local):
     # roofline of the hop step: the persistent stretch kernel (claim and commit
     # phases of every event), or claim + commit launches when it is off
     hbm, peak_kind = peaks()
-    b_alg = 14.0 + 8.0 * s_frac            # bytes per attempt
+    # algorithmic bytes per attempt: vox 4 + occupancy 2 + claim write 4 + claim
+    # read-back 4, and on success vox 4 + two occupancy writes of 2
+    b_alg = 14.0 + 8.0 * s_frac
     persistent = kt["run_events"] > 0
     n_ev = max(1, kt["claim_launches"] + kt["run_events"])
     hop_ms = kt["claim_ms"] + kt["commit_ms"] + kt["run_ms"]
@@ -566,7 +572,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": workload_name(args),
-                   "rule": args.rule, "compartments": args.compartments, "lattice": list(SHAPE), "molecules": N_MOL,
+                   "rule": args.rule, "compartments": args.compartments, "kernel": args.kernel, "lattice": list(SHAPE), "molecules": N_MOL,
                    "events_per_step": EVENTS_PER_STEP, "resort_period": RESORT_PERIOD,
                    "replicas": world, "l2": "inputs larger than L2 (occupancy 268 MB + claim words 537 MB)",
                    "parallelism": "replicas (one independent lattice per GPU)"},

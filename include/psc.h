@@ -150,7 +150,11 @@ typedef struct {
     int32_t tiles;            /* persistent stretches of a species without
                                  reactions: 1 = owner-computes tile kernel
                                  wherever it applies, -1 = never, 0 = default
-                                 (when the species has >= 2^20 molecules)      */
+                                 (when the species has >= 2^20 molecules and,
+                                 at its first stretch, the fullest box holds
+                                 at most 1.4 x the mean: molecules confined
+                                 to part of the lattice take the molecule-
+                                 list kernel, which balances itself)           */
     int32_t tile_regions;     /* tile kernel: most boxes (blocks) to cut the
                                  lattice into (0/-1 = one per SM)              */
     int32_t subvolume;        /* before populate: 1 = update rule of the

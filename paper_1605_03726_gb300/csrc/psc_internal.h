@@ -244,6 +244,8 @@ int subvol_max_blocks(int sm_count);        // co-resident 256-thread blocks of 
 int tile_smem_limit(int device);
 constexpr int kTileOutbox = 1024;           // departures a block stages per event
 constexpr int kTileQueue = 1024;            // molecules a block defers per commit phase (contested, leaving)
+// largest max / mean box load at which the automatic choice keeps the tile kernel
+constexpr double kTileMaxImbalance = 1.4;
 inline int tile_smem_bytes(const TilePlan& P)
 {
     return ((P.box_words + 3) & ~3) * 4 + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
@@ -251,6 +253,7 @@ inline int tile_smem_bytes(const TilePlan& P)
 }
 constexpr int kTileThreads = 512;
 constexpr int kTileBlocksPerSM = 2;
+void launch_tile_count(const TileArgs& A, int32_t* counts, int blocks, cudaStream_t st);
 void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st);
 void launch_tile_gather(const TileArgs& A, cudaStream_t st);

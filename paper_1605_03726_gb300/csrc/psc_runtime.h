@@ -81,6 +81,9 @@ struct psc_lattice {
     int64_t rs_max = 0;
 
     bool general[kMaxSpecies] = {};
+    // automatic stretch kernel (psc_options.tiles = 0) of species with a tile
+    // plan: 0 not decided yet, 1 the tile kernel, -1 the molecule-list kernel
+    int8_t tile_auto[kMaxSpecies] = {};
     bool live[kMaxSpecies] = {};       // takes part in a reaction: keeps its codes
     bool fo2[kMaxSpecies] = {};
     std::vector<int> reconcile[kMaxSpecies];

@@ -824,6 +824,39 @@ int tile_smem_limit(int device)
     return optin - 1024 < share ? optin - 1024 : share;
 }
 
+// molecules per region (counts[regions], zeroed by the caller): the loads the
+// plan would give the blocks
+__global__ void __launch_bounds__(1024) k_tile_count(const TileArgs A, int32_t* counts)
+{
+    extern __shared__ int s_hist[];                      // [regions] + owner tables
+    const EventArgs& a = A.ev;
+    const int R = A.plan.regions;
+    uint8_t* own = reinterpret_cast<uint8_t*>(s_hist + R);
+    const int n = *a.count;
+    tile_build_owners(A.plan, own);
+    for (int q = threadIdx.x; q < R; q += blockDim.x) s_hist[q] = 0;
+    __syncthreads();
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        int32_t i, j, k;
+        decode(a.geo, (uint32_t)a.list.vox[x], i, j, k);
+        atomicAdd(&s_hist[tile_region_of(A.plan, own, i, j, k)], 1);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < R; q += blockDim.x)
+        if (s_hist[q]) atomicAdd(&counts[q], s_hist[q]);
+}
+
+void launch_tile_count(const TileArgs& A, int32_t* counts, int blocks, cudaStream_t st)
+{
+    const int smem = A.plan.regions * (int)sizeof(int) + ((A.plan.nbi + A.plan.nbj + A.plan.nbk + 15) & ~15);
+    static int configured = 48 * 1024;
+    if (smem > configured) {
+        cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = smem;
+    }
+    k_tile_count<<<blocks, 1024, smem, st>>>(A, counts);
+}
+
 void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st)
 {
     const int smem = 2 * A.plan.regions * (int)sizeof(int) + ((A.plan.nbi + A.plan.nbj + A.plan.nbk + 15) & ~15);

@@ -170,3 +170,35 @@ def test_compartment_errors_match_oracle():
             L.populate(1)                         # more than compartment 0 holds
         assert e.value.rc == -4
         L.close()
+
+
+def test_auto_kernel_follows_box_loads():
+    # 256^3, 2^20 + 1 walkers: spread over the lattice the automatic choice
+    # takes the tile kernel; confined to a round cell (the boxes outside hold
+    # nothing, those inside about 3x the mean) it takes the molecule-list
+    # kernel.  Either way the result is the one every kernel gives.
+    shape = (256, 256, 256)
+    n = (1 << 20) + 1
+    lab = models.cell_labels(*shape, radius=200.0)
+    for confined in (False, True):
+        out = {}
+        for tiles in (0, 1, -1):
+            L = psc.Lattice(*shape, voxel_radius=1e-8)
+            if confined:
+                L.set_compartments(lab, 3)
+                L.add_species(10e-12, n, compartment=2)
+            else:
+                L.add_species(10e-12, n)
+            L.set_options(time_kernels=1, **({"tiles": tiles} if tiles else {}))
+            L.populate(4)
+            L.run_events(60)
+            kt = L.kernel_times()
+            out[tiles] = (L.coords(0), kt["tile_launches"], kt["run_launches"])
+            L.close()
+        for t in (1, -1):
+            assert np.array_equal(out[t][0][0], out[0][0][0]) and np.array_equal(out[t][0][1], out[0][0][1])
+        tile_launches, stretch_launches = out[0][1], out[0][2]     # tile stretches count as both
+        if confined:
+            assert tile_launches == 0 and stretch_launches > 0
+        else:
+            assert tile_launches > 0 and tile_launches == stretch_launches

@@ -306,7 +306,6 @@ static bool tile_balanced(psc_lattice* L, int s, const TilePlan& P)
 bool tile_plan(psc_lattice* L, int s, TilePlan* P)
 {
     if (L->opt.tiles < 0 || L->general[s] || L->live[s] || !(L->sp[s].D > 0.0)) return false;
-    if (L->bflags & PSC_FCC) return false;        // the boxes' stencil tables are the HCP ones
     if (L->opt.tiles == 0 && L->sp[s].n0 < ((int64_t)1 << 20)) return false;
     if (L->sp[s].n0 <= 0) return false;
     // periodic axes must wrap whole bricks
@@ -322,7 +321,9 @@ bool tile_plan(psc_lattice* L, int s, TilePlan* P)
     int64_t best_work = -1, best_box = 0;
     TilePlan best{};
     // owner tables, neighbourhood masks, outbox
-    const int64_t owners = ((nbi + nbj + nbk + 15) & ~15) + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4;
+    const int fcc = (L->bflags & PSC_FCC) ? 1 : 0;
+    const int64_t owners = ((nbi + nbj + nbk + 15) & ~15) + (fcc ? 96 : 32) * 8 * 4 + kTileOutbox * 12 +
+                           kTileQueue * 4;
     for (int pi = 1; pi <= std::min(std::min(nbi, S), 255); ++pi) {
         for (int pj = 1; pj <= std::min(std::min(nbj, S / pi), 255); ++pj) {
             for (int pk = 1; pk <= std::min(std::min(nbk, S / (pi * pj)), 255); ++pk) {
@@ -334,7 +335,7 @@ bool tile_plan(psc_lattice* L, int s, TilePlan* P)
                 if (best_work < 0 || work < best_work || (work == best_work && box < best_box)) {
                     best_work = work;
                     best_box = box;
-                    best = TilePlan{pi, pj, pk, nbi, nbj, nbk, ei, ej, ek, pi * pj * pk, (int32_t)box, 0};
+                    best = TilePlan{pi, pj, pk, nbi, nbj, nbk, ei, ej, ek, pi * pj * pk, (int32_t)box, 0, fcc};
                 }
             }
         }

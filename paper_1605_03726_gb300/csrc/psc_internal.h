@@ -172,6 +172,7 @@ struct TilePlan {
     int32_t regions;
     int32_t box_words;         // (ei + 2)(ej + 2)(ek + 2): region plus one brick of halo
     int32_t cap;               // molecule slots per region (bucket, inbox)
+    int32_t fcc;               // FCC lattice: stencil and neighbourhood masks by k mod 3
 };
 
 // A stretch of a species without reactions under the tile kernel.  Each
@@ -248,7 +249,7 @@ constexpr int kTileQueue = 1024;            // molecules a block defers per comm
 constexpr double kTileMaxImbalance = 1.4;
 inline int tile_smem_bytes(const TilePlan& P)
 {
-    return ((P.box_words + 3) & ~3) * 4 + 32 * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
+    return ((P.box_words + 3) & ~3) * 4 + (P.fcc ? 96 : 32) * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
            ((P.nbi + P.nbj + P.nbk + 15) & ~15);
 }
 constexpr int kTileThreads = 512;

@@ -32,7 +32,14 @@ struct TileBox {
     int bi0, bj0, bk0;         // first brick of the region
     int ei, ej, ek;            // region extent in bricks
     int BI, BJ, BK;            // box extent (region + one brick each side)
+    int zoff3;                 // FCC: global k mod 3 = (z + zoff3) mod 3 for box coordinate z; HCP: -1
 };
+
+// FCC layer class k mod 3 of box coordinate z (-1 on HCP lattices)
+__device__ __forceinline__ int tile_c3(const TileBox& b, int z)
+{
+    return b.zoff3 < 0 ? -1 : (z + b.zoff3) % 3;
+}
 
 __device__ __forceinline__ TileBox tile_box(const TilePlan& P, int r)
 {
@@ -47,6 +54,7 @@ __device__ __forceinline__ TileBox tile_box(const TilePlan& P, int r)
     b.BI = b.ei + 2;
     b.BJ = b.ej + 2;
     b.BK = b.ek + 2;
+    b.zoff3 = P.fcc ? ((2 * b.bk0 - 2) % 3 + 3) % 3 : -1;
     return b;
 }
 
@@ -214,11 +222,20 @@ __device__ __forceinline__ int64_t tile_region_word(const TilePlan& P, const Til
     return ((int64_t)(b.bk0 - 1 + wz) * P.nbj + (b.bj0 - 1 + wy)) * P.nbi + (b.bi0 - 1 + wx);
 }
 
-// Stencil offset of direction d for box coordinates (x, y, z) (Sec. 2.1)
-__device__ __forceinline__ void tile_step(int d, int y, int z, int& dx, int& dy, int& dz)
+// Stencil offset of direction d for box coordinates (x, y, z) (Sec. 2.1); on
+// FCC lattices (App. B) c3 = k mod 3 picks the j offsets and the row parity
+// (box and global coordinates share the parities of j and k: the box origin
+// is a whole number of bricks away)
+__device__ __forceinline__ void tile_step(int d, int y, int z, int c3, int& dx, int& dy, int& dz)
 {
-    const uint32_t wi = ((y + z) & 1) ? c_stencil[1] : c_stencil[0];
-    const uint32_t wj = (z & 1) ? c_stencil[3] : c_stencil[2];
+    uint32_t wi, wj;
+    if (c3 < 0) {
+        wi = ((y + z) & 1) ? c_stencil[1] : c_stencil[0];
+        wj = (z & 1) ? c_stencil[3] : c_stencil[2];
+    } else {
+        wi = ((y + (c3 == 1 ? 1 : 0)) & 1) ? c_stencil[1] : c_stencil[0];
+        wj = c_stencil[5 + c3];
+    }
     dx = (int)((wi >> (2 * d)) & 3u) - 1;
     dy = (int)((wj >> (2 * d)) & 3u) - 1;
     dz = (int)((c_stencil[4] >> (2 * d)) & 3u) - 1;
@@ -231,17 +248,19 @@ __device__ __forceinline__ void tile_step(int d, int y, int z, int& dx, int& dy,
 // holding (x - 1, y - 1, z - 1).  Only the low bits of (x, y, z) matter: the
 // stencil depends on the parities of y + z and z, and the brick steps on x & 3,
 // y & 3, z & 1.
-__device__ __forceinline__ void tile_build_nbmask(uint32_t* mask)
+__device__ __forceinline__ void tile_build_nbmask(uint32_t* mask, int fcc)
 {
-    for (int e = threadIdx.x; e < 32 * 8; e += blockDim.x) mask[e] = 0u;
+    const int entries = fcc ? 96 : 32;          // FCC: one table per layer class k mod 3
+    for (int e = threadIdx.x; e < entries * 8; e += blockDim.x) mask[e] = 0u;
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < entries) {
         const int c = threadIdx.x;
-        const int x = 4 + (c & 3), y = 4 + ((c >> 2) & 3), z = 2 + (c >> 4);
+        const int c3 = fcc ? (c >> 5) : -1;
+        const int x = 4 + (c & 3), y = 4 + ((c >> 2) & 3), z = 2 + ((c >> 4) & 1);
         const int wx0 = (x - 1) >> 2, wy0 = (y - 1) >> 2, wz0 = (z - 1) >> 1;
         for (int d = -1; d < 12; ++d) {
             int dx = 0, dy = 0, dz = 0;
-            if (d >= 0) tile_step(d, y, z, dx, dy, dz);
+            if (d >= 0) tile_step(d, y, z, c3, dx, dy, dz);
             const int nx = x + dx, ny = y + dy, nz = z + dz;
             const int q = ((nx >> 2) - wx0) | (((ny >> 2) - wy0) << 1) | (((nz >> 1) - wz0) << 2);
             mask[c * 8 + q] |= 1u << ((nx & 3) | ((ny & 3) << 2) | ((nz & 1) << 4));
@@ -254,9 +273,9 @@ __device__ __forceinline__ void tile_build_nbmask(uint32_t* mask)
 // of them is the mover, so 1 means: the target is vacant and no other
 // molecule can reach it.
 __device__ __forceinline__ int tile_nb_count(const uint32_t* box, const uint32_t* nbmask, int BI, int BIJ,
-                                             int BJ, int tx, int ty, int tz)
+                                             int BJ, int tx, int ty, int tz, int c3)
 {
-    const int c = (tx & 3) | ((ty & 3) << 2) | ((tz & 1) << 4);
+    const int c = ((tx & 3) | ((ty & 3) << 2) | ((tz & 1) << 4)) + (c3 > 0 ? 32 * c3 : 0);
     const int w0 = (((tz - 1) >> 1) * BJ + ((ty - 1) >> 2)) * BI + ((tx - 1) >> 2);
     const uint4 m0 = *reinterpret_cast<const uint4*>(nbmask + c * 8);
     const uint4 m1 = *reinterpret_cast<const uint4*>(nbmask + c * 8 + 4);
@@ -340,7 +359,7 @@ __device__ __forceinline__ bool tile_wait_neighbours(const TileArgs& A, const ui
 // Shared-memory areas of the tile kernel, after the box.
 struct TileShared {
     uint32_t* box;
-    uint32_t* nbmask;          // [32][8]
+    uint32_t* nbmask;          // [32][8], FCC [3][32][8]
     int32_t* o_t;              // outbox: departures of an event
     uint32_t* o_id;
     int32_t* o_q;
@@ -353,7 +372,7 @@ __device__ __forceinline__ TileShared tile_shared(uint32_t* smem, const TilePlan
     TileShared S;
     S.box = smem;
     S.nbmask = smem + ((P.box_words + 3) & ~3);
-    S.o_t = reinterpret_cast<int32_t*>(S.nbmask + 32 * 8);
+    S.o_t = reinterpret_cast<int32_t*>(S.nbmask + (P.fcc ? 96 : 32) * 8);
     S.o_id = reinterpret_cast<uint32_t*>(S.o_t + kTileOutbox);
     S.o_q = S.o_t + 2 * kTileOutbox;
     S.queue = S.o_t + 3 * kTileOutbox;
@@ -379,7 +398,7 @@ __device__ __forceinline__ bool tile_apply_move(const TileArgs& A, const TileBox
     const Geometry& G = A.ev.geo;
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, dx, dy, dz);
+    tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
     const int tx = x + dx, ty = y + dy, tz = z + dz;
     const int vwx = x >> 2, vwy = y >> 2, vwz = z >> 1;
     const int wv = (vwz * b.BJ + vwy) * b.BI + vwx;
@@ -469,7 +488,7 @@ __device__ __forceinline__ void tile_target_global(const Geometry& G, const Tile
 {
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, dx, dy, dz);
+    tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
     tile_global(G, b, x + dx, y + dy, z + dz, nb.i, nb.j, nb.k, nb.wrap);
     nb.t = nb.i + G.ni * (nb.j + G.nj * nb.k);
 }
@@ -509,7 +528,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
     const int rx1 = 4 + 4 * b.ei, ry1 = 4 + 4 * b.ej, rz1 = 2 + 2 * b.ek;   // region: [4, rx1) x [4, ry1) x [2, rz1)
     const FastDiv div_bi = tile_fastdiv((uint32_t)b.BI), div_bj2 = tile_fastdiv((uint32_t)(b.BJ - 2));
     tile_build_owners(A.plan, S.own);
-    tile_build_nbmask(S.nbmask);
+    tile_build_nbmask(S.nbmask, A.plan.fcc);
     // region and halo bits from the global mirror
     for (int q = threadIdx.x; q < nbox; q += blockDim.x) {
         const int wx = q % b.BI, wy = (q / b.BI) % b.BJ, wz = q / (b.BI * b.BJ);
@@ -557,10 +576,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 philox(ii[u], g, c2, 0u, a.key0, a.key1, rnd);
                 const int d = (int)__umulhi(rnd[0], 12u);
                 uint32_t st = (uint32_t)d << 26;
-                tile_step(d, y, z, dx, dy, dz);
+                tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
                 const int tx = x + dx, ty = y + dy, tz = z + dz;
                 if (tx >= xlo && tx < xhi && ty >= ylo && ty < yhi && tz >= zlo && tz < zhi) {
-                    if (tile_nb_count(box, S.nbmask, b.BI, BIJ, b.BJ, tx, ty, tz) == 1) {
+                    if (tile_nb_count(box, S.nbmask, b.BI, BIJ, b.BJ, tx, ty, tz, tile_c3(b, tz)) == 1) {
                         st |= kTileMove;                 // only the mover itself is next to the target
                     } else if (!(box[((tz >> 1) * b.BJ + (ty >> 2)) * b.BI + (tx >> 2)] &
                                  (1u << ((tx & 3) | ((ty & 3) << 2) | ((tz & 1) << 4))))) {
@@ -610,7 +629,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 if (st & kTileMove) {
                     int x, y, z, dx, dy, dz;
                     tile_unpack(w, x, y, z);
-                    tile_step((int)((st >> 26) & 15u), y, z, dx, dy, dz);
+                    tile_step((int)((st >> 26) & 15u), y, z, tile_c3(b, z), dx, dy, dz);
                     const int tx = x + dx, ty = y + dy, tz = z + dz;
                     if (tx >= 4 && tx < rx1 && ty >= 4 && ty < ry1 && tz >= 2 && tz < rz1) {
                         uint32_t neww;

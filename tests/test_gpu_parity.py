@@ -272,8 +272,8 @@ def test_tile_kernel_interleaved_species_with_crowders(claim_table):
 
 
 # FCC lattice (App. B): the per-event kernels (reactions), the molecule-list
-# persistent kernel (walkers), periodic with k a multiple of 3 and reflective
-# ragged shapes; the tile kernel does not take FCC and must fall back.
+# persistent kernel and the tile kernel (walkers), periodic with k a multiple
+# of 3 and reflective ragged shapes.
 FCC_CASES = [
     ((24, 24, 24), psc.PERIODIC_ALL | psc.FCC, "ab"),
     ((48, 40, 30), psc.PERIODIC_ALL | psc.FCC, "walk"),
@@ -298,3 +298,29 @@ def test_fcc_lattice_matches_oracle(shape, boundary, model, persistent):
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, chunk)
+
+
+# The tile kernel on FCC lattices: stencil and neighbourhood masks by layer
+# class k mod 3; periodic k a multiple of 6 (whole bricks and whole ABC
+# periods), reflective ragged shapes, one box or many, sparse to crowded.
+FCC_TILE_CASES = [
+    ((48, 44, 42), psc.PERIODIC_ALL | psc.FCC, 0.02, 0),
+    ((48, 44, 42), psc.PERIODIC_ALL | psc.FCC, 0.30, 8),
+    ((40, 36, 30), psc.PERIODIC_ALL | psc.FCC, 0.10, 1),
+    ((37, 29, 23), psc.FCC, 0.05, 0),
+    ((37, 29, 23), psc.FCC, 0.55, 5),
+    ((40, 30, 25), psc.PERIODIC_I | psc.FCC, 0.20, 0),
+]
+
+
+@pytest.mark.parametrize("claim_table", [1, 2])
+@pytest.mark.parametrize("shape,boundary,frac,regions", FCC_TILE_CASES)
+def test_tile_kernel_fcc_matches_oracle(shape, boundary, frac, regions, claim_table):
+    n = max(1, int(frac * shape[0] * shape[1] * shape[2]))
+    g, o = build_both(shape, lambda L: models.diffusion_only(L, n), 23, boundary=boundary,
+                      claim_table=claim_table, tiles=1, tile_regions=regions, time_kernels=1)
+    for chunk in (1, 7, 40):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+    assert g.kernel_times()["tile_launches"] > 0

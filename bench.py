@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--compartments", default="none", choices=["none", "cell"],
                     help="cell: the same lattice holding a round cell (outside, membrane, cytoplasm) "
                          "with the walkers in its cytoplasm")
+    ap.add_argument("--lattice", default="hcp", choices=["hcp", "fcc"],
+                    help="fcc: the same molecules on a 512 x 512 x 516 FCC lattice (k a multiple of 6 for "
+                         "periodic ABC stacking in whole bricks)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "list"],
                     help="stretch kernel: the library's choice, the tile kernel, or the molecule-list kernel")
     ap.add_argument("--rule", default="sync", choices=["sync", "subvolume"],
@@ -211,17 +214,25 @@ def profiled_traffic(name):
         return None
 
 
-_CELL = None
+_CELL = {}
+FCC_SHAPE = (512, 512, 516)
 
 
-def cell_labels():
+def lattice_shape(args):
+    return FCC_SHAPE if args.lattice == "fcc" else SHAPE
+
+
+def lattice_flags(mod, args):
+    return mod.PERIODIC_ALL | (mod.FCC if args.lattice == "fcc" else 0)
+
+
+def cell_labels(shape=SHAPE):
     """Compartments of the cell workload: an ellipsoid in index space (nominal
     spacings 2, 1.73, 1.63 voxel radii along i, j, k) of radius 400 voxel
     radii in the middle of the box; 0 outside, 1 a membrane shell 1.5 voxel
     radii thick, 2 the cytoplasm (35 % of the voxels).  Built slab by slab."""
-    global _CELL
-    if _CELL is None:
-        ni, nj, nk = SHAPE
+    if shape not in _CELL:
+        ni, nj, nk = shape
         lab = np.zeros((nk, nj, ni), dtype=np.uint8)
         j, i = np.meshgrid(np.arange(nj), np.arange(ni), indexing="ij")
         rij = (2.0 * (i - (ni - 1) / 2.0)) ** 2 + (1.73 * (j - (nj - 1) / 2.0)) ** 2
@@ -230,13 +241,13 @@ def cell_labels():
             sl = lab[k]
             sl[r < 400.0] = 1
             sl[r < 398.5] = 2
-        _CELL = lab.reshape(-1)
-    return _CELL
+        _CELL[shape] = lab.reshape(-1)
+    return _CELL[shape]
 
 
 def model(psc, L, args):
     if args.compartments == "cell":
-        L.set_compartments(cell_labels(), 3)
+        L.set_compartments(cell_labels(lattice_shape(args)), 3)
         L.add_species(D, N_MOL, compartment=2)
     else:
         L.add_species(D, N_MOL)
@@ -248,7 +259,8 @@ def model(psc, L, args):
 
 
 def make_lattice(psc, seed, device, stream, args):
-    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=device, stream=stream)
+    L = psc.Lattice(*lattice_shape(args), voxel_radius=RV, boundary=lattice_flags(psc, args), device=device,
+                    stream=stream)
     model(psc, L, args)
     L.populate(seed)
     return L
@@ -318,7 +330,7 @@ def gpu_arm(args, rank, world, local):
     tr = profiled_traffic("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
     traffic = None
     events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
-    if persistent and args.rule == "sync" and args.compartments == "none" and tr and tr.get("kernel_rev") == kernel_revision() and \
+    if persistent and args.rule == "sync" and args.compartments == "none" and args.lattice == "hcp" and tr and tr.get("kernel_rev") == kernel_revision() and \
             int(tr.get("events_per_launch", 0)) == round(events_per_launch):
         traffic = int(tr["dram_read_bytes"]) + int(tr["dram_write_bytes"])
     roofline = {
@@ -368,7 +380,7 @@ def e2e_run(psc, args, rank, local, torch, ranks):
     torch.cuda.synchronize(local)
     ranks.barrier()
     t0 = time.perf_counter()
-    L = psc.Lattice(*SHAPE, voxel_radius=RV, boundary=psc.PERIODIC_ALL, device=local)
+    L = psc.Lattice(*lattice_shape(args), voxel_radius=RV, boundary=lattice_flags(psc, args), device=local)
     model(psc, L, args)
     L.populate(replica_seed(rank))
     for _ in range(args.steps):
@@ -495,9 +507,9 @@ def oracle_lattice(seed, args):
     """The same workload on the oracle, under the same update rule."""
     import oracle
     rule = oracle.RULE_SUBVOL if args.rule == "subvolume" else oracle.RULE_SYNC
-    L = oracle.Lattice(*SHAPE, RV, oracle.PERIODIC_ALL, rule)
+    L = oracle.Lattice(*lattice_shape(args), RV, lattice_flags(oracle, args), rule)
     if args.compartments == "cell":
-        L.set_compartments(cell_labels(), 3)
+        L.set_compartments(cell_labels(lattice_shape(args)), 3)
         L.add_species(D, N_MOL, compartment=2)
     else:
         L.add_species(D, N_MOL)
@@ -524,7 +536,12 @@ def cpu_baseline(seconds, args):
 
 
 def workload_name(args):
-    return (WORKLOAD + ("; sub-volume update rule" if args.rule == "subvolume" else "") +
+    base = WORKLOAD
+    if args.lattice == "fcc":
+        base = base.replace("512^3 HCP lattice", "512 x 512 x 516 FCC lattice").replace("at 1% occupancy",
+                                                                                     "at 0.99% occupancy")
+    return (base +
+            ("; sub-volume update rule" if args.rule == "subvolume" else "") +
             ("; in a round cell (outside, membrane, cytoplasm), the walkers in its cytoplasm"
              if args.compartments == "cell" else ""))
 
@@ -545,8 +562,9 @@ def reference_arm(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_name(args), "step": "1 hop interval (oracle)", "lattice": list(SHAPE),
-                   "molecules": N_MOL, "rule": args.rule, "compartments": args.compartments},
+        "config": {"workload": workload_name(args), "step": "1 hop interval (oracle)", "lattice": list(lattice_shape(args)),
+                   "molecules": N_MOL, "rule": args.rule, "compartments": args.compartments,
+                   "lattice_kind": args.lattice},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d + %d warm-up events of the 512^3 lattice, single thread, %s"
@@ -572,7 +590,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": workload_name(args),
-                   "rule": args.rule, "compartments": args.compartments, "kernel": args.kernel, "lattice": list(SHAPE), "molecules": N_MOL,
+                   "rule": args.rule, "compartments": args.compartments, "kernel": args.kernel, "lattice": list(lattice_shape(args)),
+                   "lattice_kind": args.lattice, "molecules": N_MOL,
                    "events_per_step": EVENTS_PER_STEP, "resort_period": RESORT_PERIOD,
                    "replicas": world, "l2": "inputs larger than L2 (occupancy 268 MB + claim words 537 MB)",
                    "parallelism": "replicas (one independent lattice per GPU)"},

@@ -35,10 +35,12 @@ struct TileBox {
     int zoff3;                 // FCC: global k mod 3 = (z + zoff3) mod 3 for box coordinate z; HCP: -1
 };
 
-// FCC layer class k mod 3 of box coordinate z (-1 on HCP lattices)
+// FCC layer class k mod 3 of box coordinate z (-1 on HCP lattices, known
+// at compile time so that the HCP kernel carries no FCC code)
+template <bool FCC>
 __device__ __forceinline__ int tile_c3(const TileBox& b, int z)
 {
-    return b.zoff3 < 0 ? -1 : (z + b.zoff3) % 3;
+    return FCC ? (z + b.zoff3) % 3 : -1;
 }
 
 __device__ __forceinline__ TileBox tile_box(const TilePlan& P, int r)
@@ -392,13 +394,14 @@ __device__ __forceinline__ void tile_unpack(uint32_t w, int& x, int& y, int& z)
 // the target or needed no claim).  Updates the box and the global mirror's
 // outer layer, hands it over if it leaves the box; returns whether it stays
 // and, if so, its new packed coordinates.
+template <bool FCC>
 __device__ __forceinline__ bool tile_apply_move(const TileArgs& A, const TileBox& b, const TileShared& S, int r,
                                                 int* s_out_n, uint32_t w, uint32_t id, int d, uint32_t& neww)
 {
     const Geometry& G = A.ev.geo;
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
+    tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
     const int tx = x + dx, ty = y + dy, tz = z + dz;
     const int vwx = x >> 2, vwy = y >> 2, vwz = z >> 1;
     const int wv = (vwz * b.BJ + vwy) * b.BI + vwx;
@@ -484,11 +487,12 @@ __device__ __forceinline__ void tile_keep(bool keep, uint32_t w, uint32_t id, in
 }
 
 // Global voxel of the target of a molecule (packed w, direction d)
+template <bool FCC>
 __device__ __forceinline__ void tile_target_global(const Geometry& G, const TileBox& b, uint32_t w, int d, Nb& nb)
 {
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
+    tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
     tile_global(G, b, x + dx, y + dy, z + dz, nb.i, nb.j, nb.k, nb.wrap);
     nb.t = nb.i + G.ni * (nb.j + G.nj * nb.k);
 }
@@ -503,6 +507,7 @@ __device__ __forceinline__ void tile_publish(uint32_t* flags, int r, uint32_t va
     }
 }
 
+template <bool FCC>
 __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(const TileArgs A)
 {
     extern __shared__ uint32_t smem[];
@@ -576,10 +581,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 philox(ii[u], g, c2, 0u, a.key0, a.key1, rnd);
                 const int d = (int)__umulhi(rnd[0], 12u);
                 uint32_t st = (uint32_t)d << 26;
-                tile_step(d, y, z, tile_c3(b, z), dx, dy, dz);
+                tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
                 const int tx = x + dx, ty = y + dy, tz = z + dz;
                 if (tx >= xlo && tx < xhi && ty >= ylo && ty < yhi && tz >= zlo && tz < zhi) {
-                    if (tile_nb_count(box, S.nbmask, b.BI, BIJ, b.BJ, tx, ty, tz, tile_c3(b, tz)) == 1) {
+                    if (tile_nb_count(box, S.nbmask, b.BI, BIJ, b.BJ, tx, ty, tz, tile_c3<FCC>(b, tz)) == 1) {
                         st |= kTileMove;                 // only the mover itself is next to the target
                     } else if (!(box[((tz >> 1) * b.BJ + (ty >> 2)) * b.BI + (tx >> 2)] &
                                  (1u << ((tx & 3) | ((ty & 3) << 2) | ((tz & 1) << 4))))) {
@@ -629,11 +634,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 if (st & kTileMove) {
                     int x, y, z, dx, dy, dz;
                     tile_unpack(w, x, y, z);
-                    tile_step((int)((st >> 26) & 15u), y, z, tile_c3(b, z), dx, dy, dz);
+                    tile_step((int)((st >> 26) & 15u), y, z, tile_c3<FCC>(b, z), dx, dy, dz);
                     const int tx = x + dx, ty = y + dy, tz = z + dz;
                     if (tx >= 4 && tx < rx1 && ty >= 4 && ty < ry1 && tz >= 2 && tz < rz1) {
                         uint32_t neww;
-                        tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
+                        tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
                         w = neww;
                         ++n_hop;
                     } else {
@@ -650,13 +655,14 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                         bool win = (st & kTileMove) != 0u;
                         if (!win) {
                             Nb nb;
-                            tile_target_global(G, b, w, (int)((st >> 26) & 15u), nb);
+                            tile_target_global<FCC>(G, b, w, (int)((st >> 26) & 15u), nb);
                             win = __ldcg(&claim[nb.t]) == ii[u];
                             if (win) claim[nb.t] = kNoClaim;
                         }
                         if (win) {
                             uint32_t neww = w;
-                            keep = tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
+                            keep = tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u),
+                                                        neww);
                             w = neww;
                             ++n_hop;
                         }
@@ -686,7 +692,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                     tt[u] = -1;
                     if (!(ss[u] & kTileClaimed)) continue;
                     Nb nb;
-                    tile_target_global(G, b, vv[u], (int)((ss[u] >> 26) & 15u), nb);
+                    tile_target_global<FCC>(G, b, vv[u], (int)((ss[u] >> 26) & 15u), nb);
                     tt[u] = nb.t;
                     rb[u] = __ldcg(&claim[nb.t]);
                 }
@@ -702,7 +708,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                     }
                     if (keep && win) {
                         uint32_t neww = w;
-                        keep = tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
+                        keep = tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
                         w = neww;
                         ++n_hop;
                     }
@@ -887,19 +893,25 @@ void launch_tile_scatter(const TileArgs& A, int blocks, cudaStream_t st)
     k_tile_scatter<<<blocks, 1024, smem, st>>>(A);
 }
 
-cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st)
+template <bool FCC>
+static cudaError_t launch_tile_run_t(const TileArgs& A, cudaStream_t st)
 {
     const size_t smem = (size_t)tile_smem_bytes(A.plan);
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_tile_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_tile_run<FCC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     void* args[] = {const_cast<TileArgs*>(&A)};
-    return cudaLaunchCooperativeKernel((const void*)k_tile_run, dim3(A.plan.regions), dim3(kTileThreads), args,
+    return cudaLaunchCooperativeKernel((const void*)k_tile_run<FCC>, dim3(A.plan.regions), dim3(kTileThreads), args,
                                        smem, st);
+}
+
+cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st)
+{
+    return A.plan.fcc ? launch_tile_run_t<true>(A, st) : launch_tile_run_t<false>(A, st);
 }
 
 void launch_tile_gather(const TileArgs& A, cudaStream_t st)

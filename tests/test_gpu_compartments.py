@@ -202,3 +202,59 @@ def test_auto_kernel_follows_box_loads():
             assert tile_launches == 0 and stretch_launches > 0
         else:
             assert tile_launches > 0 and tile_launches == stretch_launches
+
+
+def test_tile_kernel_fcc_with_compartments():
+    # FCC, periodic (k a multiple of 6), walkers of three species in random
+    # compartments, forced onto the tile kernel with several box counts
+    shape = (48, 44, 42)
+    for regions in (0, 6):
+        g, o, ns = pair(shape, psc.PERIODIC_ALL | psc.FCC, random_walkers(shape, seed=5), 14,
+                        tiles=1, tile_regions=regions, time_kernels=1)
+        for chunk in (1, 9, 40):
+            g.run_events(chunk)
+            o.run_events(chunk)
+            same(g, o, ns, chunk)
+        assert g.kernel_times()["tile_launches"] > 0
+        g.close()
+        o.close()
+
+
+def test_autotuned_cell_matches_untuned():
+    # the tuner's trials are real events: a tuned cell lattice ends where an
+    # untuned one ends after as many events, and both stay with the oracle
+    shape = (96, 96, 96)
+    recipe = cell(shape, 75.0, 8000, 3000, 2000, 8000)
+    T = psc.Lattice(*shape, voxel_radius=1e-8, boundary=0)
+    U = psc.Lattice(*shape, voxel_radius=1e-8, boundary=0)
+    o = oracle.Lattice(*shape, 1e-8, 0, oracle.RULE_SYNC)
+    for L in (T, U, o):
+        recipe(L)
+        L.populate(17)
+    r = T.autotune(600)
+    assert 0 < r["events"] <= 600
+    U.run_events(r["events"])
+    o.run_events(r["events"])
+    same(T, o, 5, "tuned")
+    same(U, o, 5, "untuned")
+    T.run_events(150)
+    o.run_events(150)
+    same(T, o, 5, "after")
+    for L in (T, U, o):
+        L.close()
+
+
+def test_device_bytes_count_one_mirror_per_compartment():
+    shape = (64, 64, 64)
+    lab = models.cell_labels(*shape, radius=50.0)
+    sizes = []
+    for n_comp in (None, 3):
+        L = psc.Lattice(*shape, voxel_radius=1e-8)
+        if n_comp:
+            L.set_compartments(lab, n_comp)
+        L.add_species(1e-12, 1000, compartment=2 if n_comp else None)
+        L.populate(1)
+        sizes.append(L.device_bytes())
+        L.close()
+    words = (64 // 4) * (64 // 4) * (64 // 2)
+    assert sizes[1] - sizes[0] == 2 * words * 4

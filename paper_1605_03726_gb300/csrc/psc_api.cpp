@@ -995,8 +995,10 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
         int threads = 0, blocks = 0;
         const int per = run_width(L, s, &threads, &blocks);
         TilePlan plan{};
-        const bool tiles = per > 0 && tile_plan(L, s, &plan);
-        if (per > 0) {
+        // the tile kernel needs no molecule slots per thread: it also takes
+        // species above the molecule-list kernel's capacity
+        const bool tiles = L->opt.persistent > 0 && !L->general[s] && tile_plan(L, s, &plan);
+        if (per > 0 || tiles) {
             // how long does species s stay next?  (Tile stretches keep their
             // own spatial order: no re-sort points.)
             const uint32_t g0 = L->g;

@@ -822,15 +822,18 @@ __global__ void __launch_bounds__(THREADS, MINB) k_hop_run(const RunArgs r)
 }
 
 // Launch shapes: two 768-thread blocks per SM (<= 42 registers) with up to 6
-// molecules per thread, or one 768-thread block per SM with up to 24
-// (3 x 24 x 768 words = 216 KB of shared memory).  More resident threads
+// molecules per thread, or one 768-thread block per SM with up to 16
+// (3 x 16 x 768 words = 144 KB of shared memory).  More resident threads
 // beat more molecules in flight per thread here (measured: the kernel is
-// bound by L2 operations, not by per-thread latency chains).
+// bound by L2 operations, not by per-thread latency chains).  With 16
+// molecules per thread it only matches one claim and one commit launch per
+// event, and with 24 it took 1.85 times as long (2.2M molecules at 512^3),
+// so larger species take the per-event launches (or the tile kernel).
 struct RunShape {
     int per_thread, threads, blocks_per_sm;
 };
 static const RunShape kRunShapes[] = {
-    {2, 768, 2}, {4, 768, 2}, {6, 768, 2}, {8, 768, 1}, {12, 768, 1}, {16, 768, 1}, {24, 768, 1}};
+    {2, 768, 2}, {4, 768, 2}, {6, 768, 2}, {8, 768, 1}, {12, 768, 1}, {16, 768, 1}};
 
 int run_capacity(int64_t n, int* threads_per_block, int* blocks, int sm_count, int min_per_thread)
 {
@@ -872,7 +875,6 @@ static cudaError_t launch_run_h(const RunArgs& r, int blocks, int threads, int p
     case 8: return launch_run_t<HASH, 8, 768, 1>(r, blocks, threads, st);
     case 12: return launch_run_t<HASH, 12, 768, 1>(r, blocks, threads, st);
     case 16: return launch_run_t<HASH, 16, 768, 1>(r, blocks, threads, st);
-    case 24: return launch_run_t<HASH, 24, 768, 1>(r, blocks, threads, st);
     default: return cudaErrorInvalidValue;
     }
 }

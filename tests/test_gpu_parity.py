@@ -324,3 +324,28 @@ def test_tile_kernel_fcc_matches_oracle(shape, boundary, frac, regions, claim_ta
         o.run_events(chunk)
         assert_same(g, o, chunk)
     assert g.kernel_times()["tile_launches"] > 0
+
+
+def test_tile_kernel_above_molecule_list_capacity():
+    # 256^3 periodic at 25 % occupancy: 4,194,304 walkers, more than the
+    # molecule-list kernel holds (16 per thread); the tile kernel takes them
+    # by default, the per-event kernels when stretches are off
+    shape = (256, 256, 256)
+    n = 256 ** 3 // 4
+    o = oracle.Lattice(*shape, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
+    models.diffusion_only(o, n)
+    o.populate(8)
+    o.run_events(6)
+    for persistent in (0, -1):
+        g = psc.Lattice(*shape, voxel_radius=1e-8)
+        models.diffusion_only(g, n)
+        g.set_options(time_kernels=1, **({"persistent": persistent} if persistent else {}))
+        g.populate(8)
+        g.run_events(6)
+        assert_same(g, o, persistent)
+        kt = g.kernel_times()
+        if persistent == 0:
+            assert kt["tile_events"] == 6
+        else:
+            assert kt["tile_events"] == 0 and kt["claim_launches"] == 6
+        g.close()

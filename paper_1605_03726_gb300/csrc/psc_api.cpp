@@ -459,19 +459,21 @@ int enqueue_subvol(psc_lattice* L, int s, int64_t n_events)
     cudaStream_t st = L->stream;
     SubvolArgs A{};
     A.ev = event_args(L, s);
-    A.word[0] = L->subvol.word[0];
-    A.word[1] = L->subvol.word[1];
-    A.done = L->subvol.done;
-    A.won = L->subvol.won;
-    A.alone = L->subvol.alone;
-    A.count = L->subvol.count;
+    A.word = L->subvol.word;
+    A.head = L->subvol.head;
+    A.next = L->subvol.next;
+    A.state = L->subvol.state;
+    A.colour0 = L->subvol.colour0;
+    A.lead = L->subvol.lead;
+    A.lead_vox = L->subvol.lead_vox;
+    A.counters = L->subvol.counters;
     A.n_events = (int32_t)n_events;
     A.barrier = L->barrier;
     A.barrier_timeout_ns = (uint64_t)L->opt.barrier_timeout_us * 1000ull;
     A.barrier_phantom = (uint32_t)L->opt.barrier_phantom;
     int rc = cuda_fail(L, cudaMemsetAsync(L->barrier, 0, sizeof(BarrierState), st));
     if (rc) return rc;
-    if ((rc = cuda_fail(L, cudaMemsetAsync(L->subvol.count, 0, 3 * sizeof(uint32_t), st)))) return rc;
+    if ((rc = cuda_fail(L, cudaMemsetAsync(L->subvol.counters, 0, 32 * sizeof(uint32_t), st)))) return rc;
     cudaEvent_t sp = span_open(L);
     rc = cuda_fail(L, launch_subvol(A, L->subvol.blocks, 256, st));
     span_close(L, sp, kSpanRun, n_events);
@@ -869,20 +871,23 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     if (L->opt.subvolume > 0) {
         auto& SV = L->subvol;
         const size_t nsub = (size_t)((L->ni + 1) / 2) * (size_t)((L->nj + 1) / 2) * (size_t)((L->nk + 1) / 2);
-        SV.word[0] = (uint32_t*)dev_alloc(L, nsub * 4);
-        SV.word[1] = (uint32_t*)dev_alloc(L, nsub * 4);
-        SV.done = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
-        SV.won = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
-        SV.alone = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
-        SV.count = (uint32_t*)dev_alloc(L, 16);
-        if (!SV.word[0] || !SV.word[1] || !SV.done || !SV.won || !SV.alone || !SV.count) return PSC_E_NOMEM;
+        SV.word = (uint32_t*)dev_alloc(L, nsub * 4);
+        SV.head = (uint32_t*)dev_alloc(L, nsub * 4);
+        SV.next = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.state = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.colour0 = (uint8_t*)dev_alloc(L, (size_t)max_mobile);
+        SV.lead = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.lead_vox = (uint32_t*)dev_alloc(L, (size_t)max_mobile * 4);
+        SV.counters = (uint32_t*)dev_alloc(L, 32 * 4);
+        if (!SV.word || !SV.head || !SV.next || !SV.state || !SV.colour0 || !SV.lead || !SV.lead_vox ||
+            !SV.counters)
+            return PSC_E_NOMEM;
+        SV.subvols = (int64_t)nsub;
+        SV.slots = max_mobile;
         SV.blocks = subvol_max_blocks(L->sm_count);
         if (SV.blocks <= 0) return PSC_E_CUDA;
-        launch_fill_u32(SV.word[0], kNoClaim, nsub, L->sm_count * 4, L->stream);
-        launch_fill_u32(SV.word[1], kNoClaim, nsub, L->sm_count * 4, L->stream);
-        int rcs;
-        if ((rcs = cuda_fail(L, cudaMemsetAsync(SV.done, 0, (size_t)max_mobile * 4, L->stream)))) return rcs;
-        if ((rcs = cuda_fail(L, cudaMemsetAsync(SV.won, 0, (size_t)max_mobile * 4, L->stream)))) return rcs;
+        launch_fill_u32(SV.word, kNoClaim, nsub, L->sm_count * 4, L->stream);
+        launch_fill_u32(SV.head, kNoClaim, nsub, L->sm_count * 4, L->stream);
     }
 
     cudaStream_t st = L->stream;
@@ -1335,6 +1340,8 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
     } else {
         b += 2 * N * 16 + 2 * N * 8;
     }
+    // sub-volume rule buffers
+    b += L->subvol.subvols * 8 + L->subvol.slots * 17 + (L->subvol.counters ? 128 : 0);
     // tile kernel buffers, once a stretch has used them
     const auto& T = L->tile;
     b += T.slots * 4 * 5 + (int64_t)T.regions * 4 * 4 + T.ids * 8;

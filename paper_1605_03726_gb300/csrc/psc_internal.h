@@ -206,11 +206,14 @@ struct TileArgs {
 // sub-volume scheme on the lattice; species without reactions).
 struct SubvolArgs {
     EventArgs ev;              // g = index of the first event
-    uint32_t* word[2];         // per 2x2x2 sub-volume: lowest id still to go (by round parity)
-    uint32_t* done;            // per list slot: 1 + index of the event that processed it
-    uint32_t* won;             // per list slot: 1 + sub-volume it won last round (its word is reset next round)
-    uint32_t* alone;           // per list slot: alone in its sub-volume at the round's phase A
-    uint32_t* count;           // [3] candidates per round, rotating
+    uint32_t* word;            // per 2x2x2 sub-volume: lowest waiting id of the colour's turn (kNoClaim: free)
+    uint32_t* head;            // per sub-volume: first list slot of its chain of waiting molecules (kNoClaim: none)
+    uint32_t* next;            // per list slot: the next slot of its sub-volume's chain
+    uint32_t* state;           // per list slot: its sub-volume at the event's start, bit 31 it leads it, bit 30 alone
+    uint8_t* colour0;          // per list slot: colour of its sub-volume when the event began
+    uint32_t* lead;            // per list slot: the leaders' slots, colour by colour (top bit: alone)
+    uint32_t* lead_vox;        // per list slot: the voxel of an alone leader, in the same order
+    uint32_t* counters;        // [2][16] by event parity: molecules and leaders per colour
     int32_t n_events;
     BarrierState* barrier;
     uint64_t barrier_timeout_ns;

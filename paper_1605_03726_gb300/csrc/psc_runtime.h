@@ -122,11 +122,15 @@ struct psc_lattice {
 
     // sub-volume rule buffers (allocated at populate when the rule is on)
     struct SubvolBuffers {
-        uint32_t* word[2] = {nullptr, nullptr};
-        uint32_t* done = nullptr;
-        uint32_t* won = nullptr;
-        uint32_t* alone = nullptr;
-        uint32_t* count = nullptr;
+        uint32_t* word = nullptr;
+        uint32_t* head = nullptr;
+        uint32_t* next = nullptr;
+        uint32_t* state = nullptr;
+        uint8_t* colour0 = nullptr;
+        uint32_t* lead = nullptr;
+        uint32_t* lead_vox = nullptr;
+        uint32_t* counters = nullptr;
+        int64_t subvols = 0, slots = 0;
         int blocks = 0;
     } subvol;
 };

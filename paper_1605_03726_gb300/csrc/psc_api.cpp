@@ -1119,26 +1119,61 @@ static int read_list(psc_lattice* L, int32_t s, std::vector<int32_t>& vox, std::
     return PSC_OK;
 }
 
+// The number of molecules of species s, for a call that only sizes its buffers
+static int list_size(psc_lattice* L, int32_t s, int64_t* n_out)
+{
+    int rc = check_device(L);
+    if (rc) return rc;
+    int32_t n = 0;
+    if ((rc = cuda_fail(L, cudaMemcpy(&n, &L->sc->counts[s], 4, cudaMemcpyDeviceToHost)))) return rc;
+    L->d2h += 4;
+    *n_out = n;
+    return n > 0 ? PSC_E_ARG : PSC_OK;
+}
+
+// Read-out order by molecule id.  Ids are never reused, so when the ids of a
+// list span exactly as many values as it has entries (every species without
+// reactions keeps the ids placement gave it) each entry goes straight to
+// its place; otherwise they are sorted.
+static void order_by_id(const std::vector<uint32_t>& ids, std::vector<int64_t>& order)
+{
+    const int64_t n = (int64_t)ids.size();
+    order.assign((size_t)n, -1);
+    if (n == 0) return;
+    const auto mm = std::minmax_element(ids.begin(), ids.end());
+    const uint32_t lo = *mm.first;
+    bool placed = (int64_t)*mm.second - (int64_t)lo + 1 == n;
+    for (int64_t a = 0; placed && a < n; ++a) {
+        int64_t& slot = order[ids[a] - lo];
+        if (slot >= 0) placed = false;                   // a repeated id: sort instead
+        slot = a;
+    }
+    if (placed) return;
+    for (int64_t a = 0; a < n; ++a) order[a] = a;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+}
+
 int psc_coords(psc_lattice* L, int32_t s, int32_t* ijk, uint32_t* ids_out, int64_t cap, int64_t* n_out)
 {
     if (!L || !n_out || s < 0 || s >= L->nsp) return PSC_E_ARG;
     if (!L->populated) return PSC_E_ORDER;
     DevGuard dg(L->device);
+    if (!ijk || cap <= 0) return list_size(L, s, n_out);
     std::vector<int32_t> vox;
     std::vector<uint32_t> ids;
     int rc = read_list(L, s, vox, ids, nullptr);
     if (rc) return rc;
     const int64_t n = (int64_t)vox.size();
     *n_out = n;
-    if (n > cap || (n > 0 && !ijk)) return PSC_E_ARG;
-    std::vector<int64_t> order(n);
-    for (int64_t a = 0; a < n; ++a) order[a] = a;
-    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+    if (n > cap) return PSC_E_ARG;
+    std::vector<int64_t> order;
+    order_by_id(ids, order);
+    const uint32_t ni = (uint32_t)L->ni, nj = (uint32_t)L->nj;
     for (int64_t a = 0; a < n; ++a) {
-        const int64_t v = vox[order[a]];
-        ijk[3 * a + 0] = (int32_t)(v % L->ni);
-        ijk[3 * a + 1] = (int32_t)((v / L->ni) % L->nj);
-        ijk[3 * a + 2] = (int32_t)(v / ((int64_t)L->ni * L->nj));
+        const uint32_t v = (uint32_t)vox[order[a]], q = v / ni;
+        ijk[3 * a + 0] = (int32_t)(v - q * ni);
+        ijk[3 * a + 1] = (int32_t)(q % nj);
+        ijk[3 * a + 2] = (int32_t)(q / nj);
         if (ids_out) ids_out[a] = ids[order[a]];
     }
     return PSC_OK;
@@ -1149,6 +1184,7 @@ int psc_unwrapped(psc_lattice* L, int32_t s, int32_t* xyz, uint32_t* ids_out, in
     if (!L || !n_out || s < 0 || s >= L->nsp) return PSC_E_ARG;
     if (!L->populated) return PSC_E_ORDER;
     DevGuard dg(L->device);
+    if (!xyz || cap <= 0) return list_size(L, s, n_out);
     std::vector<int32_t> vox;
     std::vector<uint32_t> ids;
     std::vector<uint64_t> img;
@@ -1156,15 +1192,14 @@ int psc_unwrapped(psc_lattice* L, int32_t s, int32_t* xyz, uint32_t* ids_out, in
     if (rc) return rc;
     const int64_t n = (int64_t)vox.size();
     *n_out = n;
-    if (n > cap || (n > 0 && !xyz)) return PSC_E_ARG;
-    std::vector<int64_t> order(n);
-    for (int64_t a = 0; a < n; ++a) order[a] = a;
-    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
+    if (n > cap) return PSC_E_ARG;
+    std::vector<int64_t> order;
+    order_by_id(ids, order);
+    const uint32_t ni = (uint32_t)L->ni, nj = (uint32_t)L->nj;
     for (int64_t a = 0; a < n; ++a) {
-        const int64_t v = vox[order[a]];
+        const uint32_t v = (uint32_t)vox[order[a]], q = v / ni;
         const uint64_t w = img[order[a]];
-        const int32_t i = (int32_t)(v % L->ni), j = (int32_t)((v / L->ni) % L->nj),
-                      k = (int32_t)(v / ((int64_t)L->ni * L->nj));
+        const int32_t i = (int32_t)(v - q * ni), j = (int32_t)(q % nj), k = (int32_t)(q / nj);
         const int32_t I = i + (int32_t)(int16_t)(w & 0xFFFF) * L->ni;
         const int32_t J = j + (int32_t)(int16_t)((w >> 16) & 0xFFFF) * L->nj;
         const int32_t K = k + (int32_t)(int16_t)((w >> 32) & 0xFFFF) * L->nk;

@@ -396,7 +396,7 @@ def e2e_run(psc, args, rank, local, torch, ranks):
     return {"value": job_throughput(args.steps * EVENTS_PER_STEP * N_MOL, ranks.world, wall_ms), "unit": UNIT,
             "h2d_bytes_per_step": int(st["h2d_bytes"] // steps),
             "d2h_bytes_per_step": int(st["d2h_bytes"] // steps),
-            "includes": "lattice create + populate (placement sort of 134M voxels) + K steps, "
+            "includes": "lattice create + populate (placement keys of all 134M voxels) + K steps, "
                         "counts read to host after every step, final positions read to host"}
 
 

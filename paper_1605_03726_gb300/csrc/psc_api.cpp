@@ -684,22 +684,19 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     int64_t N = 0;
     for (int s = 0; s < L->nsp; ++s) N += L->sp[s].n0;
     if (N > L->V) return PSC_E_FULL;
-    // compartments: room in each, products that can land in theirs, and the
-    // first sorted voxel of each species (species of one compartment take its
-    // voxels one after another, in species order)
+    // compartments: room in each for its species, and products that can land
+    // in theirs
     const bool comps = !L->labels.empty();
-    int64_t start[kMaxSpecies] = {};
+    int64_t start[kMaxSpecies] = {};                 // first sorted voxel of each species (placement)
     {
-        int64_t room[kMaxCompartments] = {}, base[kMaxCompartments + 1] = {}, used[kMaxCompartments] = {};
+        int64_t room[kMaxCompartments] = {}, used[kMaxCompartments] = {};
         if (comps) {
             for (int64_t v = 0; v < L->V; ++v) room[L->labels[v]]++;
         } else {
             room[0] = L->V;
         }
-        for (int c = 0; c < L->ncomp; ++c) base[c + 1] = base[c] + room[c];
         for (int s = 0; s < L->nsp; ++s) {
             const int c = L->sp[s].comp;
-            start[s] = base[c] + used[c];
             used[c] += L->sp[s].n0;
             if (used[c] > room[c]) return PSC_E_FULL;
         }
@@ -919,32 +916,81 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     for (int t = 0; t < 2; ++t)
         if (L->tables[t]) launch_fill_u64(L->tables[t], kEmptySlot, (size_t)1 << hb_max, fill_blocks, st);
 
-    // ---- placement: voxels sorted by (Philox key, voxel) dealt to the species ----
+    // ---- placement (Sec. 3.4): voxels in (Philox key, voxel) order, per
+    // compartment, dealt to the species.  Only the first voxels of each
+    // compartment matter: a histogram of the keys' top bits finds the bin
+    // that covers them, and only the voxels up to it are sorted (by voxel,
+    // then stably by key, then by compartment). ----
     if (N > 0) {
-        uint32_t* keys = (uint32_t*)dev_alloc(L, V * 4);
-        uint32_t* vals = (uint32_t*)dev_alloc(L, V * 4);
-        void* scratch = dev_alloc(L, sort_scratch_bytes(L->V));
-        if (!keys || !vals || !scratch) return PSC_E_NOMEM;
+        const int nc = comps ? L->ncomp : 1;
+        const int bins = 1 << kPlaceBits;
+        int64_t need[kMaxCompartments] = {};
+        for (int s = 0; s < L->nsp; ++s) need[comps ? L->sp[s].comp : 0] += L->sp[s].n0;
+        uint32_t* hist = (uint32_t*)dev_alloc(L, (size_t)nc * bins * 4);
+        int32_t* pick_n = (int32_t*)dev_alloc(L, 4);
+        if (!hist || !pick_n) return PSC_E_NOMEM;
+        if ((rc = cuda_fail(L, cudaMemsetAsync(hist, 0, (size_t)nc * bins * 4, st)))) return rc;
+        if ((rc = cuda_fail(L, cudaMemsetAsync(pick_n, 0, 4, st)))) return rc;
+        launch_place_hist((uint32_t)V, (uint32_t)seed, (uint32_t)(seed >> 32), labels_d, nc, hist, fill_blocks, st);
+        std::vector<uint32_t> h((size_t)nc * bins);
+        if ((rc = cuda_fail(L, cudaMemcpyAsync(h.data(), hist, h.size() * 4, cudaMemcpyDeviceToHost, st)))) return rc;
+        if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
+        L->d2h += h.size() * 4;
+        PlaceLimits lim;
+        int64_t cand[kMaxCompartments] = {}, cbase[kMaxCompartments + 1] = {};
+        for (int c = 0; c < kMaxCompartments; ++c) lim.bin[c] = -1;
+        for (int c = 0; c < nc; ++c) {
+            int64_t cum = 0;
+            for (int b = 0; b < bins && need[c] > 0; ++b) {
+                cum += h[(size_t)c * bins + b];
+                if (cum >= need[c]) { lim.bin[c] = b; break; }
+            }
+            if (need[c] > 0 && lim.bin[c] < 0) return PSC_E_FULL;      // cannot happen: room was checked
+            cand[c] = need[c] > 0 ? cum : 0;
+            cbase[c + 1] = cbase[c] + cand[c];
+        }
+        const int64_t M = cbase[nc];
+        {
+            int64_t used[kMaxCompartments] = {};
+            for (int s = 0; s < L->nsp; ++s) {
+                const int c = comps ? L->sp[s].comp : 0;
+                start[s] = cbase[c] + used[c];
+                used[c] += L->sp[s].n0;
+            }
+        }
+        uint32_t* cvox = (uint32_t*)dev_alloc(L, (size_t)M * 4);
+        uint32_t* ckey = (uint32_t*)dev_alloc(L, (size_t)M * 4);
+        void* scratch = dev_alloc(L, sort_scratch_bytes(M));
+        if (!cvox || !ckey || !scratch) return PSC_E_NOMEM;
         SortScratch ss;
-        sort_scratch_bind(ss, scratch, L->V);
-        launch_populate_keys(keys, vals, (uint32_t)V, (uint32_t)seed, (uint32_t)(seed >> 32), fill_blocks, st);
-        if (radix_sort_pairs(keys, vals, nullptr, L->V, L->V, 32, ss, st, &L->launches) != 0)
+        sort_scratch_bind(ss, scratch, M);
+        launch_place_pick((uint32_t)V, (uint32_t)seed, (uint32_t)(seed >> 32), labels_d, lim, cvox, ckey, pick_n,
+                          (int32_t)M, &L->sc->err, fill_blocks, st);
+        int vbits = 1;
+        while (vbits < 31 && ((int64_t)1 << vbits) < L->V) ++vbits;
+        if (radix_sort_pairs(cvox, ckey, nullptr, M, M, vbits, ss, st, &L->launches) != 0 ||
+            radix_sort_pairs(ckey, cvox, nullptr, M, M, 32, ss, st, &L->launches) != 0)
             return cuda_fail(L, cudaErrorUnknown);
         if (comps) {
-            // stable pass on the compartment: (compartment, key, voxel) order
-            launch_label_keys(vals, labels_d, keys, L->V, fill_blocks, st);
-            if (radix_sort_pairs(keys, vals, nullptr, L->V, L->V, 8, ss, st, &L->launches) != 0)
+            launch_label_keys(cvox, labels_d, ckey, M, fill_blocks, st);
+            if (radix_sort_pairs(ckey, cvox, nullptr, M, M, 8, ss, st, &L->launches) != 0)
                 return cuda_fail(L, cudaErrorUnknown);
             L->launches += 1;
         }
         int64_t off[kMaxSpecies + 1];
         off[0] = 0;
         for (int s = 0; s < L->nsp; ++s) off[s + 1] = off[s] + L->sp[s].n0;
-        launch_populate_scatter(vals, N, off, start, L->nsp, L->occ, L->geo, L->model_d, fill_blocks, st);
+        launch_populate_scatter(cvox, N, off, start, L->nsp, L->occ, L->geo, L->model_d, fill_blocks, st);
+        L->launches += 3;
+        int32_t picked = 0;
+        if ((rc = cuda_fail(L, cudaMemcpyAsync(&picked, pick_n, 4, cudaMemcpyDeviceToHost, st)))) return rc;
         if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;
-        dev_free_one(L, keys);
-        dev_free_one(L, vals);
+        if (picked != M) return PSC_E_CUDA;                             // the two passes disagree
+        dev_free_one(L, cvox);
+        dev_free_one(L, ckey);
         dev_free_one(L, scratch);
+        dev_free_one(L, hist);
+        dev_free_one(L, pick_n);
     }
     if (labels_d) {
         if ((rc = cuda_fail(L, cudaStreamSynchronize(st)))) return rc;

@@ -264,6 +264,18 @@ void launch_tile_gather(const TileArgs& A, cudaStream_t st);
 // mirror c of n: bit v set where labels[v] != c (walls), the rest clear
 void launch_mirror_walls(uint32_t* bits0, uint64_t words, int n, const uint8_t* labels, const Geometry& geo,
                          int blocks, cudaStream_t st);
+// placement by selection (psc_populate): per compartment, a histogram of the
+// top kPlaceBits bits of the voxels' placement keys, then the voxels whose
+// key bin is at most that compartment's limit (-1: none), in no order
+constexpr int kPlaceBits = 10;
+struct PlaceLimits {
+    int32_t bin[kMaxCompartments];
+};
+void launch_place_hist(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, int nc, uint32_t* hist,
+                       int blocks, cudaStream_t st);
+void launch_place_pick(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, const PlaceLimits& lim,
+                       uint32_t* out_vox, uint32_t* out_key, int32_t* count, int32_t cap, int32_t* err, int blocks,
+                       cudaStream_t st);
 // keys[r] = labels[vals[r]]: the compartment of each sorted voxel
 void launch_label_keys(const uint32_t* vals, const uint8_t* labels, uint32_t* keys, int64_t n, int blocks,
                        cudaStream_t st);
@@ -277,8 +289,6 @@ void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStrea
 void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
 void launch_births(const EventArgs& a, cudaStream_t st);
 void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
-void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
-                          int blocks, cudaStream_t st);
 // molecule r (ids in species order, species s owning [offsets[s],
 // offsets[s+1])) takes sorted_vox[starts[s] + r - offsets[s]]; its bit goes
 // to the mirror of its species' compartment

@@ -1149,21 +1149,72 @@ void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t*
     k_scatter_codes<<<blocks, 256, 0, st>>>(out, list, count, code);
 }
 
-// placement key of every voxel: word 0 of Philox(seed; v, 0, 1, 0)
-__global__ void k_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1)
+// Placement by selection.  The key of voxel v is word 0 of Philox(seed; v, 0,
+// 1, 0); the species take the first voxels of each compartment in (key,
+// voxel) order, so only the voxels whose key lies in
+// the bins that cover them need sorting.  Pass 1 histograms the top
+// kPlaceBits bits of every voxel's key per compartment; pass 2 keeps the
+// voxels up to each compartment's last needed bin.
+__global__ void k_place_hist(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, int nc,
+                             uint32_t* hist)
 {
+    extern __shared__ uint32_t s_bins[];
+    const int nb = nc << kPlaceBits;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s_bins[b] = 0u;
+    __syncthreads();
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
         uint32_t u[4];
         philox(v, 0u, kTagPopulate, 0u, key0, key1, u);
-        keys[v] = u[0];
-        vals[v] = v;
+        const int c = labels ? (int)labels[v] : 0;
+        atomicAdd(&s_bins[(c << kPlaceBits) | (int)(u[0] >> (32 - kPlaceBits))], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (s_bins[b]) atomicAdd(&hist[b], s_bins[b]);
+}
+
+void launch_place_hist(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, int nc, uint32_t* hist,
+                       int blocks, cudaStream_t st)
+{
+    const int smem = (nc << kPlaceBits) * (int)sizeof(uint32_t);
+    static int configured = 48 * 1024;
+    if (smem > configured) {
+        cudaFuncSetAttribute(k_place_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = smem;
+    }
+    k_place_hist<<<blocks, 256, smem, st>>>(V, key0, key1, labels, nc, hist);
+}
+
+__global__ void k_place_pick(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, PlaceLimits lim,
+                             uint32_t* out_vox, uint32_t* out_key, int32_t* count, int32_t cap, int32_t* err)
+{
+    for (uint32_t v0 = blockIdx.x * blockDim.x; v0 < V; v0 += gridDim.x * blockDim.x) {   // whole warps
+        const uint32_t v = v0 + threadIdx.x;
+        bool want = false;
+        uint32_t key = 0u;
+        if (v < V) {
+            uint32_t u[4];
+            philox(v, 0u, kTagPopulate, 0u, key0, key1, u);
+            key = u[0];
+            want = (int)(key >> (32 - kPlaceBits)) <= lim.bin[labels ? (int)labels[v] : 0];
+        }
+        const int slot = warp_alloc(count, want);
+        if (want) {
+            if (slot < cap) {
+                out_vox[slot] = v;
+                out_key[slot] = key;
+            } else {
+                atomicOr(err, kErrListOverflow);
+            }
+        }
     }
 }
 
-void launch_populate_keys(uint32_t* keys, uint32_t* vals, uint32_t V, uint32_t key0, uint32_t key1,
-                          int blocks, cudaStream_t st)
+void launch_place_pick(uint32_t V, uint32_t key0, uint32_t key1, const uint8_t* labels, const PlaceLimits& lim,
+                       uint32_t* out_vox, uint32_t* out_key, int32_t* count, int32_t cap, int32_t* err, int blocks,
+                       cudaStream_t st)
 {
-    k_populate_keys<<<blocks, 256, 0, st>>>(keys, vals, V, key0, key1);
+    k_place_pick<<<blocks, 256, 0, st>>>(V, key0, key1, labels, lim, out_vox, out_key, count, cap, err);
 }
 
 struct Offsets {

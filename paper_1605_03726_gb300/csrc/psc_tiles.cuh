@@ -173,9 +173,24 @@ __device__ __forceinline__ void tile_refresh_halo(const Geometry& G, const TileP
     }
 }
 
+// Claim-phase decision of a molecule: bit 31 it claimed its target, bit 30
+// it hops without a claim, bits 24-29 its step (dx + 1) | (dy + 1) << 2 |
+// (dz + 1) << 4, so the commit phase needs no second stencil look-up.
 constexpr uint32_t kTileClaimed = 0x80000000u;
 constexpr uint32_t kTileMove = 0x40000000u;
-constexpr uint32_t kTileSlotMask = 0x03FFFFFFu;     // tables of at most 2^26 slots
+
+__device__ __forceinline__ uint32_t tile_pack_step(int dx, int dy, int dz)
+{
+    return (uint32_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << 24;
+}
+
+__device__ __forceinline__ void tile_step_of(uint32_t st, int& dx, int& dy, int& dz)
+{
+    const uint32_t q = st >> 24;
+    dx = (int)(q & 3u) - 1;
+    dy = (int)((q >> 2) & 3u) - 1;
+    dz = (int)((q >> 4) & 3u) - 1;
+}
 
 // Molecules in a bucket are stored by their coordinates relative to the
 // region's first voxel, x | y << 11 | z << 22 (regions of at most 2048 x 2048
@@ -390,18 +405,17 @@ __device__ __forceinline__ void tile_unpack(uint32_t w, int& x, int& y, int& z)
     z = (int)(w >> 22) + 2;
 }
 
-// A molecule of the box (packed coordinates w) hops in direction d (it won
-// the target or needed no claim).  Updates the box and the global mirror's
-// outer layer, hands it over if it leaves the box; returns whether it stays
-// and, if so, its new packed coordinates.
-template <bool FCC>
+// A molecule of the box (packed coordinates w) takes the step its decision
+// st holds (it won the target or needed no claim).  Updates the box and the
+// global mirror's outer layer, hands it over if it leaves the box; returns
+// whether it stays and, if so, its new packed coordinates.
 __device__ __forceinline__ bool tile_apply_move(const TileArgs& A, const TileBox& b, const TileShared& S, int r,
-                                                int* s_out_n, uint32_t w, uint32_t id, int d, uint32_t& neww)
+                                                int* s_out_n, uint32_t w, uint32_t id, uint32_t st, uint32_t& neww)
 {
     const Geometry& G = A.ev.geo;
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
+    tile_step_of(st, dx, dy, dz);
     const int tx = x + dx, ty = y + dy, tz = z + dz;
     const int vwx = x >> 2, vwy = y >> 2, vwz = z >> 1;
     const int wv = (vwz * b.BJ + vwy) * b.BI + vwx;
@@ -486,13 +500,13 @@ __device__ __forceinline__ void tile_keep(bool keep, uint32_t w, uint32_t id, in
     }
 }
 
-// Global voxel of the target of a molecule (packed w, direction d)
-template <bool FCC>
-__device__ __forceinline__ void tile_target_global(const Geometry& G, const TileBox& b, uint32_t w, int d, Nb& nb)
+// Global voxel of the target of a molecule (packed w, decision st)
+__device__ __forceinline__ void tile_target_global(const Geometry& G, const TileBox& b, uint32_t w, uint32_t st,
+                                                   Nb& nb)
 {
     int x, y, z, dx, dy, dz;
     tile_unpack(w, x, y, z);
-    tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
+    tile_step_of(st, dx, dy, dz);
     tile_global(G, b, x + dx, y + dy, z + dz, nb.i, nb.j, nb.k, nb.wrap);
     nb.t = nb.i + G.ni * (nb.j + G.nj * nb.k);
 }
@@ -580,8 +594,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 uint32_t rnd[4];
                 philox(ii[u], g, c2, 0u, a.key0, a.key1, rnd);
                 const int d = (int)__umulhi(rnd[0], 12u);
-                uint32_t st = (uint32_t)d << 26;
                 tile_step(d, y, z, tile_c3<FCC>(b, z), dx, dy, dz);
+                uint32_t st = tile_pack_step(dx, dy, dz);
                 const int tx = x + dx, ty = y + dy, tz = z + dz;
                 if (tx >= xlo && tx < xhi && ty >= ylo && ty < yhi && tz >= zlo && tz < zhi) {
                     if (tile_nb_count(box, S.nbmask, b.BI, BIJ, b.BJ, tx, ty, tz, tile_c3<FCC>(b, tz)) == 1) {
@@ -634,11 +648,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                 if (st & kTileMove) {
                     int x, y, z, dx, dy, dz;
                     tile_unpack(w, x, y, z);
-                    tile_step((int)((st >> 26) & 15u), y, z, tile_c3<FCC>(b, z), dx, dy, dz);
+                    tile_step_of(st, dx, dy, dz);
                     const int tx = x + dx, ty = y + dy, tz = z + dz;
                     if (tx >= 4 && tx < rx1 && ty >= 4 && ty < ry1 && tz >= 2 && tz < rz1) {
                         uint32_t neww;
-                        tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
+                        tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], st, neww);
                         w = neww;
                         ++n_hop;
                     } else {
@@ -655,14 +669,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                         bool win = (st & kTileMove) != 0u;
                         if (!win) {
                             Nb nb;
-                            tile_target_global<FCC>(G, b, w, (int)((st >> 26) & 15u), nb);
+                            tile_target_global(G, b, w, st, nb);
                             win = __ldcg(&claim[nb.t]) == ii[u];
                             if (win) claim[nb.t] = kNoClaim;
                         }
                         if (win) {
                             uint32_t neww = w;
-                            keep = tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u),
-                                                        neww);
+                            keep = tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], st, neww);
                             w = neww;
                             ++n_hop;
                         }
@@ -692,7 +705,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                     tt[u] = -1;
                     if (!(ss[u] & kTileClaimed)) continue;
                     Nb nb;
-                    tile_target_global<FCC>(G, b, vv[u], (int)((ss[u] >> 26) & 15u), nb);
+                    tile_target_global(G, b, vv[u], ss[u], nb);
                     tt[u] = nb.t;
                     rb[u] = __ldcg(&claim[nb.t]);
                 }
@@ -708,7 +721,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_run(con
                     }
                     if (keep && win) {
                         uint32_t neww = w;
-                        keep = tile_apply_move<FCC>(A, b, S, r, &s_misc[2], w, ii[u], (int)((st >> 26) & 15u), neww);
+                        keep = tile_apply_move(A, b, S, r, &s_misc[2], w, ii[u], st, neww);
                         w = neww;
                         ++n_hop;
                     }

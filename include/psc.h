@@ -121,8 +121,15 @@ typedef struct {
     int32_t block_threads;    /* threads per block of the event kernels (256)   */
     int32_t blocks_per_sm;    /* resident blocks per SM for grid sizing (8)     */
     int32_t collect_stats;    /* 1 = count attempts/hops/... (default 0), -1 off */
-    int32_t graph_events;     /* >0: replay runs of this many single-species
-                                 events from a captured CUDA graph (default 0) */
+    int32_t graph_events;     /* >= 2: runs of this many events that take
+                                 per-event launches (species with reactions,
+                                 or persistent = -1) are captured in a CUDA
+                                 graph the second time their pattern (species
+                                 in order, claim-table state, re-sort
+                                 counters) comes up and replayed from then
+                                 on, the event index read from device memory;
+                                 same results, fewer launches.  Off while
+                                 time_kernels is on (default 0 = off)          */
     int32_t time_kernels;     /* 1 = record CUDA events around the kernels of
                                  every event (psc_kernel_times_get), -1 off     */
     int32_t claim_table;      /* before populate: 1 = one claim word per voxel,

@@ -122,6 +122,11 @@ EventArgs event_args(const psc_lattice* L, int s)
     a.key0 = (uint32_t)L->seed;
     a.key1 = (uint32_t)(L->seed >> 32);
     a.g = L->g;
+    a.g_base = nullptr;
+    if (L->capture_g0 >= 0) {                         // captured for replay: index relative to the run's first
+        a.g = L->g - (uint32_t)L->capture_g0;
+        a.g_base = &L->sc->g_base;
+    }
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;
@@ -1007,6 +1012,153 @@ int psc_populate(psc_lattice* L, uint64_t seed)
 
 namespace psc_rt {
 
+void graph_cache_clear(psc_lattice* L)
+{
+    for (auto& G : L->graphs)
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+    L->graphs.clear();
+    L->graph_seen.clear();
+}
+
+// Runs of per-event launches replayed from CUDA graphs (psc_options.
+// graph_events = K; small lattices, where launching dominates).  The next K
+// events are planned with the scheduler; all must take per-event launches.
+// Their pattern -- species in order, the claim tables' parity and fill, the
+// re-sort counters -- fixes every launch but the event index, which the
+// kernels then read from device memory.  A pattern met for the first time
+// runs as usual; met again it is captured once and replayed from then on,
+// the host bookkeeping advanced from what the capture recorded.  Any failure
+// to capture turns graphs off for the lattice and leaves the events to the
+// ordinary path.  *done = events queued (0: none, take one the ordinary way).
+static int graph_run(psc_lattice* L, double t_end, int64_t room, int64_t* done)
+{
+    *done = 0;
+    const int K = L->opt.graph_events;
+    if (K < 2 || room < K || L->opt.time_kernels > 0 || (int64_t)L->g + K >= (int64_t)UINT32_MAX) return PSC_OK;
+    uint64_t next[kMaxSpecies];
+    for (int s = 0; s < L->nsp; ++s) next[s] = L->sp[s].done;
+    std::vector<int> seq((size_t)K);
+    std::vector<double> at((size_t)K);
+    for (int e = 0; e < K; ++e) {
+        int best = -1;
+        double tb = 0.0;
+        for (int s = 0; s < L->nsp; ++s) {
+            if (!(L->sp[s].D > 0.0)) continue;
+            const double t = (double)(next[s] + 1) * L->sp[s].tau;
+            if (best < 0 || t < tb) { best = s; tb = t; }
+        }
+        if (best < 0 || tb > t_end) return PSC_OK;
+        if (!L->general[best] && L->opt.persistent > 0) return PSC_OK;   // a stretch comes first
+        seq[(size_t)e] = best;
+        at[(size_t)e] = tb;
+        next[best]++;
+    }
+    std::vector<uint8_t> key;
+    auto put = [&key](const void* p, size_t n) {
+        const uint8_t* b = static_cast<const uint8_t*>(p);
+        key.insert(key.end(), b, b + n);
+    };
+    bool in_run[kMaxSpecies] = {};
+    for (int s2 : seq) {
+        key.push_back((uint8_t)s2);
+        in_run[s2] = true;
+    }
+    const uint32_t parity = L->g & 1u;
+    put(&parity, 4);
+    put(L->table_used, sizeof(L->table_used));
+    for (int s = 0; s < L->nsp; ++s)                 // only the run's species can re-sort in it
+        if (in_run[s]) put(&L->since_resort[s], sizeof(uint64_t));
+    auto advance = [&](int e) {
+        L->sp[seq[(size_t)e]].done++;
+        L->g++;
+        L->clock = at[(size_t)e];
+    };
+    for (const auto& G : L->graphs) {
+        if (G.key != key) continue;
+        launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+        int rc = cuda_fail(L, cudaGraphLaunch(G.exec, L->stream));
+        if (rc) return rc;
+        for (int e = 0; e < K; ++e) advance(e);
+        L->table_used[0] = G.table_used[0];
+        L->table_used[1] = G.table_used[1];
+        for (int s = 0; s < L->nsp; ++s)
+            if (in_run[s]) L->since_resort[s] = G.since[(size_t)s];
+        L->launches += G.launches + 1;
+        L->events += (uint64_t)K;
+        *done = K;
+        return PSC_OK;
+    }
+    if (std::find(L->graph_seen.begin(), L->graph_seen.end(), key) == L->graph_seen.end()) {
+        if (L->graph_seen.size() >= 32) L->graph_seen.erase(L->graph_seen.begin());
+        L->graph_seen.push_back(key);
+        for (int e = 0; e < K; ++e) {
+            int rc = enqueue_event(L, seq[(size_t)e]);
+            if (rc) return rc;
+            advance(e);
+        }
+        *done = K;
+        return PSC_OK;
+    }
+    // seen before: capture once
+    uint64_t done0[kMaxSpecies], since0[kMaxSpecies];
+    for (int s = 0; s < L->nsp; ++s) { done0[s] = L->sp[s].done; since0[s] = L->since_resort[s]; }
+    const uint32_t g0 = L->g, used0[2] = {L->table_used[0], L->table_used[1]};
+    const double clock0 = L->clock;
+    const int64_t launches0 = L->launches;
+    const uint64_t events0 = L->events;
+    const int sticky0 = L->sticky;
+    auto restore = [&]() {
+        for (int s = 0; s < L->nsp; ++s) { L->sp[s].done = done0[s]; L->since_resort[s] = since0[s]; }
+        L->g = g0;
+        L->table_used[0] = used0[0];
+        L->table_used[1] = used0[1];
+        L->clock = clock0;
+        L->launches = launches0;
+        L->events = events0;
+        L->sticky = sticky0;
+        L->opt.graph_events = 0;
+        cudaGetLastError();
+    };
+    if (cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        restore();
+        return PSC_OK;
+    }
+    L->capture_g0 = g0;
+    int rc = PSC_OK;
+    for (int e = 0; e < K && rc == PSC_OK; ++e) {
+        rc = enqueue_event(L, seq[(size_t)e]);
+        advance(e);
+    }
+    L->capture_g0 = -1;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(L->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == PSC_OK && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PSC_OK || ce != cudaSuccess || !exec) {
+        if (exec) cudaGraphExecDestroy(exec);
+        restore();
+        return PSC_OK;
+    }
+    psc_lattice::GraphRun G;
+    G.key = key;
+    G.exec = exec;
+    G.table_used[0] = L->table_used[0];
+    G.table_used[1] = L->table_used[1];
+    G.since.assign(L->since_resort, L->since_resort + L->nsp);
+    G.launches = L->launches - launches0;
+    if (L->graphs.size() >= 8) {
+        cudaGraphExecDestroy(L->graphs.front().exec);
+        L->graphs.erase(L->graphs.begin());
+    }
+    L->graphs.push_back(std::move(G));
+    launch_fill_u32(&L->sc->g_base, g0, 1, 1, L->stream);
+    if ((rc = cuda_fail(L, cudaGraphLaunch(exec, L->stream)))) return rc;
+    L->launches += 1;
+    *done = K;
+    return PSC_OK;
+}
+
 // Queue events in scheduler order until max_events are queued or the next
 // event lies after t_end.  Consecutive events of one species without
 // reactions are grouped into persistent stretches (cut at re-sort points).
@@ -1085,6 +1237,15 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
                 if (rc) return rc;
             }
             continue;
+        }
+        if (L->opt.graph_events > 1) {
+            int64_t done = 0;
+            int rc = graph_run(L, t_end, max_events - queued, &done);
+            if (rc) return rc;
+            if (done > 0) {
+                queued += done;
+                continue;
+            }
         }
         int rc = enqueue_event(L, s);
         if (rc) return rc;
@@ -1335,6 +1496,7 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
     if (o->block_threads && (o->block_threads < 32 || o->block_threads > 256 || (o->block_threads & 31)))
         return PSC_E_ARG;
     if (o->blocks_per_sm < 0 || o->graph_events < 0) return PSC_E_ARG;
+    graph_cache_clear(L);                            // captured launches follow the options
     if (o->resort_period) L->opt.resort_period = o->resort_period;
     if (o->block_threads) L->opt.block_threads = o->block_threads;
     if (o->blocks_per_sm) L->opt.blocks_per_sm = o->blocks_per_sm;
@@ -1439,6 +1601,7 @@ void psc_lattice_destroy(psc_lattice* L)
         if (L->stream) cudaStreamSynchronize(L->stream);
         for (const auto& sp : L->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
         for (cudaEvent_t ev : L->event_pool) cudaEventDestroy(ev);
+        graph_cache_clear(L);
         dev_free_all(L);
         if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     }

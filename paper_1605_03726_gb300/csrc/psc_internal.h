@@ -106,7 +106,7 @@ struct Scalars {
     uint32_t next_id;                // next fresh molecule id
     int32_t births;                  // births queued in the current event
     int32_t err;                     // kErr* bits
-    int32_t pad;
+    uint32_t g_base;                 // index of the first event of a replayed graph
     unsigned long long stats[kNumStats];
 };
 
@@ -144,7 +144,8 @@ struct EventArgs {
     Birth* births;
     int32_t births_cap;
     uint32_t key0, key1;       // Philox key = seed
-    uint32_t g;                // global event index
+    uint32_t g;                // global event index (with g_base: its offset from *g_base)
+    const uint32_t* g_base;    // null, or the device word holding the index a replayed graph starts at
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;

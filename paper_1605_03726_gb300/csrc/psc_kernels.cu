@@ -435,10 +435,17 @@ __device__ __forceinline__ void claim_body(const EventArgs& a, uint32_t g, int b
     }
 }
 
+// the event index: in a replayed graph, the graph's first index plus the
+// event's place in it
+__device__ __forceinline__ uint32_t event_index(const EventArgs& a)
+{
+    return a.g_base ? __ldcg(a.g_base) + a.g : a.g;
+}
+
 template <bool GENERAL, bool HASH>
 __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
 {
-    claim_body<GENERAL, HASH>(a, a.g, blockIdx.x, gridDim.x);
+    claim_body<GENERAL, HASH>(a, event_index(a), blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -567,7 +574,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
 template <bool GENERAL, bool HASH>
 __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
 {
-    commit_body<GENERAL, HASH>(a, a.g, blockIdx.x, gridDim.x);
+    commit_body<GENERAL, HASH>(a, event_index(a), blockIdx.x, gridDim.x);
 }
 
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)

@@ -101,6 +101,20 @@ struct psc_lattice {
     int sticky = PSC_OK;
     std::vector<void*> allocs;
 
+    // per-event runs replayed from CUDA graphs (psc_options.graph_events):
+    // graphs by run pattern, patterns seen once, and the first event index
+    // of a run being captured (-1: none)
+    struct GraphRun {
+        std::vector<uint8_t> key;
+        cudaGraphExec_t exec = nullptr;
+        uint32_t table_used[2] = {0, 0};
+        std::vector<uint64_t> since;
+        int64_t launches = 0;
+    };
+    std::vector<GraphRun> graphs;
+    std::vector<std::vector<uint8_t>> graph_seen;
+    int64_t capture_g0 = -1;
+
     // tile kernel buffers (allocated on first use, grown when a plan needs more)
     struct TileBuffers {
         int64_t slots = 0;             // regions x cap
@@ -152,6 +166,8 @@ bool next_event(const psc_lattice* L, int* s_out, double* t_out);
 int check_device(psc_lattice* L);
 // queue events in scheduler order until max_events or the next event lies after t_end
 int drive(psc_lattice* L, double t_end, int64_t max_events);
+// drop every captured graph (launch options changed)
+void graph_cache_clear(psc_lattice* L);
 // Morton re-sort of species s's list (queued on the lattice's stream)
 int resort(psc_lattice* L, int s);
 void dev_free_one(psc_lattice* L, void* p);

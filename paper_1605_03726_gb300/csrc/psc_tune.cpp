@@ -27,6 +27,7 @@ struct Trial {
 
 void apply(psc_lattice* L, const Trial& t)
 {
+    graph_cache_clear(L);
     L->opt.persistent = t.persistent;
     L->opt.run_per_thread = t.run_per_thread;
     L->opt.block_threads = t.block_threads;

@@ -157,7 +157,8 @@ typedef struct {
     int32_t tiles;            /* persistent stretches of a species without
                                  reactions: 1 = owner-computes tile kernel
                                  wherever it applies, -1 = never, 0 = default
-                                 (when the species has >= 2^20 molecules and,
+                                 (when the species has >= 2^18 molecules on a
+                                 lattice of more than 2^22 voxels and,
                                  at its first stretch, the fullest box holds
                                  at most 1.4 x the mean: molecules confined
                                  to part of the lattice take the molecule-

@@ -311,7 +311,11 @@ static bool tile_balanced(psc_lattice* L, int s, const TilePlan& P)
 bool tile_plan(psc_lattice* L, int s, TilePlan* P)
 {
     if (L->opt.tiles < 0 || L->general[s] || L->live[s] || !(L->sp[s].D > 0.0)) return false;
-    if (L->opt.tiles == 0 && L->sp[s].n0 < ((int64_t)1 << 20)) return false;
+    // automatic choice: the tile kernel wins from about 2^18 molecules on
+    // lattices whose claims go to hash tables; on lattices of up to 2^22
+    // voxels the molecule-list kernel's per-voxel claim words stay in L2 and
+    // it wins at every density (measured on 128^3, 256^3 and 512^3)
+    if (L->opt.tiles == 0 && (L->sp[s].n0 < ((int64_t)1 << 18) || L->V <= ((int64_t)1 << 22))) return false;
     if (L->sp[s].n0 <= 0) return false;
     // periodic axes must wrap whole bricks
     if ((L->bflags & PSC_PERIODIC_I) && (L->ni & 3)) return false;

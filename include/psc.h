@@ -317,8 +317,10 @@ int psc_set_options(psc_lattice *L, const psc_options *opt);
  * kernel with 0 (fewest that fit), 8 or 16 molecules per thread, or off, and
  * the Morton re-sort period (16 .. 512 events or
  * none; each of these trials starts from freshly sorted lists and spans at
- * least two periods).  Each trial times a window of events with CUDA events
- * on the lattice's stream.  The options change only how the work is laid
+ * least two periods); and, where events take per-event launches, replay
+ * from CUDA graphs of 32 or 128 events or none (each trial first runs three
+ * runs' worth of events so that its patterns are captured).  Each trial
+ * times a window of events with CUDA events on the lattice's stream.  The options change only how the work is laid
  * out on the GPU, never the results (Sec. 2.3's synchronous rule resolves
  * every event from its snapshot and the lowest id), so the trials are real
  * events: the lattice advances by out->events events (at most max_events)
@@ -335,6 +337,7 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t resort_period;     /* -1 = no re-sort                            */
     int32_t tiles;             /* 1 tile kernel, -1 molecule-list kernel     */
+    int32_t graph_events;      /* 0 = no graph replay                        */
     int32_t trials;            /* configurations timed                       */
     int64_t events;            /* events the trials ran                      */
     double  us_per_event;      /* of the chosen configuration                */

@@ -56,7 +56,8 @@ class KernelTimes(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int32), ("run_per_thread", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("resort_period", ctypes.c_int32), ("tiles", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("resort_period", ctypes.c_int32), ("tiles", ctypes.c_int32), ("graph_events", ctypes.c_int32),
+                ("trials", ctypes.c_int32),
                 ("events", ctypes.c_int64),
                 ("us_per_event", ctypes.c_double), ("us_per_event_before", ctypes.c_double)]
 

@@ -22,7 +22,7 @@ using namespace psc_rt;
 namespace {
 
 struct Trial {
-    int32_t persistent, run_per_thread, block_threads, blocks_per_sm, resort_period, tiles;
+    int32_t persistent, run_per_thread, block_threads, blocks_per_sm, resort_period, tiles, graph_events;
 };
 
 void apply(psc_lattice* L, const Trial& t)
@@ -34,12 +34,13 @@ void apply(psc_lattice* L, const Trial& t)
     L->opt.blocks_per_sm = t.blocks_per_sm;
     L->opt.resort_period = t.resort_period;
     L->opt.tiles = t.tiles;
+    L->opt.graph_events = t.graph_events;
 }
 
 Trial current(const psc_lattice* L)
 {
     return {L->opt.persistent, L->opt.run_per_thread, L->opt.block_threads, L->opt.blocks_per_sm,
-            L->opt.resort_period, L->opt.tiles};
+            L->opt.resort_period, L->opt.tiles, L->opt.graph_events};
 }
 
 struct Timer {
@@ -157,8 +158,8 @@ extern "C" int psc_autotune(psc_lattice* L, int64_t max_events, psc_tune_result*
         // 2. persistent stretches: the tile kernel, or molecules per thread of
         //    the molecule-list kernel, or none
         if (any_run) {
-            const Trial cand[] = {{1, 0, 0, 0, 0, 1}, {1, 0, 0, 0, 0, -1}, {1, 8, 0, 0, 0, -1}, {1, 16, 0, 0, 0, -1},
-                                  {-1, 0, 0, 0, 0, -1}};
+            const Trial cand[] = {{1, 0, 0, 0, 0, 1, 0}, {1, 0, 0, 0, 0, -1, 0}, {1, 8, 0, 0, 0, -1, 0},
+                                  {1, 16, 0, 0, 0, -1, 0}, {-1, 0, 0, 0, 0, -1, 0}};
             for (const Trial& c : cand) {
                 if (rc || T.budget <= 0) break;
                 Trial t = best;
@@ -189,6 +190,32 @@ extern "C" int psc_autotune(psc_lattice* L, int64_t max_events, psc_tune_result*
             if (!rc && us < p_best_us) { p_best = t; p_best_us = us; }
         }
         if (!rc && p_best_us < INFINITY) { best = p_best; best_us = p_best_us; }
+        // 4. graph replay of per-event runs, where events take per-event
+        //    launches (species with reactions, or stretches off): a trial
+        //    first runs three runs' worth of events, so that its patterns are
+        //    seen and captured, then times a window of at least two runs
+        bool per_event = best.persistent <= 0;
+        for (int s = 0; s < L->nsp; ++s)
+            if (L->sp[s].D > 0.0 && L->general[s]) per_event = true;
+        if (per_event) {
+            const int32_t ks[] = {0, 32, 128};
+            double g_best_us = INFINITY;
+            Trial g_best = best;
+            for (int32_t k : ks) {
+                if (rc || T.budget <= 0) break;
+                const int64_t warm = 3 * (int64_t)std::max<int32_t>(k, 1);
+                const int64_t window = std::max<int64_t>(W, 2 * (int64_t)k);
+                if (warm + window > T.budget) continue;
+                Trial t = best;
+                t.graph_events = k;
+                apply(L, t);
+                if ((rc = T.warm(warm))) break;
+                double us;
+                rc = T.timed(window, &us);
+                if (!rc && us < g_best_us) { g_best = t; g_best_us = us; }
+            }
+            if (!rc && g_best_us < INFINITY) { best = g_best; best_us = g_best_us; }
+        }
     }
     apply(L, best);
     L->opt.time_kernels = saved_timing;
@@ -200,6 +227,7 @@ extern "C" int psc_autotune(psc_lattice* L, int64_t max_events, psc_tune_result*
     out->blocks_per_sm = best.blocks_per_sm;
     out->resort_period = best.resort_period;
     out->tiles = best.tiles;
+    out->graph_events = best.graph_events;
     out->trials = T.trials;
     out->events = T.ran;
     out->us_per_event = best_us;

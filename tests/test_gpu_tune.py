@@ -92,3 +92,26 @@ def test_tuned_batch_matches_solo_runs():
             a, b = m.coords(sp), s.coords(sp)
             assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     B.close()
+
+
+def test_tuned_small_reaction_lattice_with_graph_trials():
+    # 64^3 A + B -> C: launch-bound, so the tuner also tries CUDA-graph replay
+    # of per-event runs; whatever it picks, the lattice stays with the oracle
+    shape = (64, 64, 64)
+    g = psc.Lattice(*shape, voxel_radius=1e-8)
+    o = oracle.Lattice(*shape, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
+    for L in (g, o):
+        models.reaction_diffusion_ab(L, 2000, 2000)
+        L.populate(12)
+    r = g.autotune(4000)
+    assert r["graph_events"] in (0, 32, 128)
+    assert 0 < r["events"] <= 4000
+    g.run_events(700)
+    o.run_events(r["events"] + 700)
+    assert g.event_index() == o.event_index()
+    assert np.array_equal(g.grid(), o.grid())
+    for s in range(3):
+        a, b = g.coords(s), o.coords(s)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    print("tuned:", r)
+    g.close()

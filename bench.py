@@ -281,6 +281,8 @@ def gpu_arm(args, rank, world, local):
     for _ in range(args.warmup):
         L.run_events(EVENTS_PER_STEP)
     L.synchronize()
+    x0, _ = L.unwrapped(0)                 # for the displacement over the timed steps
+    t0_sim = L.time()
 
     # timed region: K steps on the library's stream, CUDA events on that stream
     L.set_options(time_kernels=1)
@@ -306,6 +308,16 @@ def gpu_arm(args, rank, world, local):
 
     elapsed_ms = ranks.max(elapsed_ms)
     value = job_throughput(args.steps * EVENTS_PER_STEP * N_MOL, world, elapsed_ms)
+
+    # mean squared displacement over the timed steps against 6 D t (App. C): in
+    # the integer basis |dr|^2 = r_v^2 (dX^2 + dY^2 / 3 + 8 dZ^2 / 3); every
+    # hop moves 2 r_v, so on the lattice MSD / 6Dt is the fraction of hops
+    # that succeed (walls of a compartment bound it further)
+    x1, _ = L.unwrapped(0)
+    d = x1.astype(np.int64) - x0.astype(np.int64)
+    msd = float(np.mean(3 * d[:, 0] ** 2 + d[:, 1] ** 2 + 8 * d[:, 2] ** 2)) / 3.0 * RV * RV
+    t_sim = L.time() - t0_sim
+    msd_ratio = msd / (6.0 * D * t_sim) if t_sim > 0 else None
 
     # success fraction of the hops, from a short counted run after the timed region
     L.set_options(collect_stats=1)
@@ -355,7 +367,10 @@ def gpu_arm(args, rank, world, local):
     }
     L.close()
     res = {"value": value, "elapsed_ms": elapsed_ms, "roofline": roofline, "clocks": clocks,
-           "gpu_launches": int(launches)}
+           "gpu_launches": int(launches),
+           "physics": {"msd_over_6Dt": round(msd_ratio, 5) if msd_ratio is not None else None,
+                       "hop_success": round(s_frac, 5), "events": args.steps * EVENTS_PER_STEP,
+                       "simulated_s": t_sim}}
 
     if not args.no_e2e:
         res["e2e"] = e2e_run(psc, args, rank, local, torch, ranks)
@@ -597,6 +612,7 @@ def main():
                    "parallelism": "replicas (one independent lattice per GPU)"},
         "roofline": res["roofline"],
         "gpu_launches": res["gpu_launches"],
+        "physics": res["physics"],
         "clocks": res["clocks"],
     }
     if "e2e" in res:

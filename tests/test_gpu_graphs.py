@@ -91,3 +91,27 @@ def test_graphs_replay_and_follow_option_changes():
     same(state(L, 3), state(U, 3), "timed")
     L.close()
     U.close()
+
+
+def test_graph_replay_with_compartments_and_fcc():
+    # the membrane-receptor cell (reactions across compartments, births into
+    # the cytoplasm) on HCP and FCC lattices: graphs or not, the same lattice
+    lab_shape = [((40, 36, 32), 0), ((37, 29, 23), psc.FCC)]
+    for shape, bnd in lab_shape:
+        lab = models.cell_labels(*shape, radius=28.0 if bnd == 0 else 24.0)
+        runs = {}
+        for graphs in (0, 16):
+            L = psc.Lattice(*shape, voxel_radius=1e-8, boundary=bnd)
+            L.set_options(resort_period=16, **({"graph_events": graphs} if graphs else {}))
+            models.receptor_binding(L, lab, 1200, 500, n_x=300, n_outside=1000, koff=2e3)
+            L.populate(3)
+            L.run_events(40)
+            L.run_events(400)
+            runs[graphs] = state(L, 5)
+            L.close()
+        same(runs[0], runs[16], shape)
+        o = oracle.Lattice(*shape, 1e-8, bnd, oracle.RULE_SYNC)
+        models.receptor_binding(o, lab, 1200, 500, n_x=300, n_outside=1000, koff=2e3)
+        o.populate(3)
+        o.run_events(440)
+        assert np.array_equal(o.grid(), runs[16][0])

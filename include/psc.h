@@ -133,7 +133,9 @@ typedef struct {
     int32_t time_kernels;     /* 1 = record CUDA events around the kernels of
                                  every event (psc_kernel_times_get), -1 off     */
     int32_t claim_table;      /* before populate: 1 = one claim word per voxel,
-                                 2 = hash table of claims, 0/-1 = by size      */
+                                 2 = hash table of claims, 0/-1 = by size (a
+                                 word per voxel up to 2^22 voxels, or where
+                                 the two tables would be as large)             */
     int32_t persistent;       /* 1 = run stretches of events of a species without
                                  reactions in one cooperative launch (default),
                                  -1 = one claim + commit launch per event       */

@@ -838,6 +838,10 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         if (L->sp[s].D > 0.0 && hb > hb_max) hb_max = hb;
     }
     bool direct = L->V <= (1ll << 22) || hb_max == 0;
+    // tables at least as large as a word per voxel buy nothing, and the
+    // per-event kernels empty the previous table in full every event (species
+    // that are reaction products get lists sized for the lattice)
+    if (2.0 * 8.0 * (double)(1ll << hb_max) >= 4.0 * (double)L->V) direct = true;
     if (L->opt.claim_table == 1) direct = true;
     if (L->opt.claim_table == 2 && hb_max > 0) direct = false;
     if (direct) {

@@ -127,6 +127,9 @@ EventArgs event_args(const psc_lattice* L, int s)
         a.g = L->g - (uint32_t)L->capture_g0;
         a.g_base = &L->sc->g_base;
     }
+    a.dirty[0] = L->dirty[0];
+    a.dirty[1] = L->dirty[1];
+    a.dirty_words = L->dirty_words;
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;
@@ -190,6 +193,14 @@ ReconcileArgs reconcile_args(const psc_lattice* L, int x)
     r.tmp = L->tmp;
     r.model = L->model_d;
     r.sc = L->sc;
+    r.dirty[0] = L->dirty[0];
+    r.dirty[1] = L->dirty[1];
+    r.g = L->g;
+    r.g_base = nullptr;
+    if (L->capture_g0 >= 0) {
+        r.g = L->g - (uint32_t)L->capture_g0;
+        r.g_base = &L->sc->g_base;
+    }
     return r;
 }
 
@@ -215,7 +226,7 @@ int enqueue_event(psc_lattice* L, int s)
         const ReconcileArgs r = reconcile_args(L, x);
         const int rb = event_blocks(L, L->cap[x]);
         launch_reconcile(r, rb, threads, L->stream);
-        launch_copyback(r, rb, threads, L->stream);
+        launch_fill(r, L->stream);
         L->launches += 2;
     }
     if (L->fo2[s]) {
@@ -813,6 +824,11 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     L->mirror_n = nwords;
     L->occ = (uint16_t*)dev_alloc(L, V * sizeof(uint16_t));
     L->bits = (uint32_t*)dev_alloc(L, nwords * nmirror * sizeof(uint32_t));
+    L->dirty_words = (uint32_t)((nwords + 31) / 32);
+    for (int x = 0; x < 2; ++x) {
+        L->dirty[x] = (uint32_t*)dev_alloc(L, (size_t)L->dirty_words * 4);
+        if (!L->dirty[x]) return PSC_E_NOMEM;
+    }
     L->sc = (Scalars*)dev_alloc(L, sizeof(Scalars));
     L->model_d = (ModelDev*)dev_alloc(L, sizeof(ModelDev));
     L->barrier = (BarrierState*)dev_alloc(L, sizeof(BarrierState));
@@ -911,6 +927,8 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     sh.next_id = (uint32_t)N;
     if ((rc = cuda_fail(L, cudaMemcpyAsync(L->sc, &sh, sizeof(sh), cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_fail(L, cudaMemsetAsync(L->occ, 0, V * sizeof(uint16_t), st)))) return rc;
+    for (int x = 0; x < 2; ++x)
+        if ((rc = cuda_fail(L, cudaMemsetAsync(L->dirty[x], 0, (size_t)L->dirty_words * 4, st)))) return rc;
     const int fill_blocks = L->sm_count * 8;
     uint8_t* labels_d = nullptr;
     if (comps) {
@@ -1573,7 +1591,8 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
 {
     if (!L || !bytes) return PSC_E_ARG;
     const int64_t mirrors = L->labels.empty() ? 1 : L->ncomp;
-    int64_t b = L->V * 2 + (int64_t)mirror_words(L->ni, L->nj, L->nk) * 4 * mirrors + (int64_t)sizeof(Scalars) +
+    const int64_t mwords = (int64_t)mirror_words(L->ni, L->nj, L->nk);
+    int64_t b = L->V * 2 + mwords * 4 * mirrors + 2 * ((mwords + 31) / 32) * 4 + (int64_t)sizeof(Scalars) +
                 (int64_t)sizeof(ModelDev);
     if (L->claim) b += L->V * 4;
     b += 2 * L->table_slots * 8;

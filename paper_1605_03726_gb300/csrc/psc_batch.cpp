@@ -95,14 +95,14 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
             BatchItem& it = bl.item[bl.n++];
             it.rep = acts[a].slot;
             it.sel = rec[k];
-            it.g = 0;
+            it.g = L->g;                  // the event's parity picks the commit's dirty map
             it.block0 = total;
             total += item_blocks(B, L->cap[rec[k]]);
         }
         if (bl.n == 0) break;
         bl.total_blocks = total;
         launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
-        launch_copyback_batch(B->tmpl_rc, bl, B->threads, B->stream);
+        launch_fill_batch(B->tmpl_rc, bl, B->stream);
         B->launches += 2;
     }
     bl.n = 0;

@@ -146,6 +146,8 @@ struct EventArgs {
     uint32_t key0, key1;       // Philox key = seed
     uint32_t g;                // global event index (with g_base: its offset from *g_base)
     const uint32_t* g_base;    // null, or the device word holding the index a replayed graph starts at
+    uint32_t* dirty[2];        // by event parity: a bit per mirror word whose voxels changed species
+    uint32_t dirty_words;      // words of one dirty map
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;
@@ -227,9 +229,12 @@ struct ReconcileArgs {
     const uint32_t* bits;
     int32_t x;                 // species whose list is reconciled
     SpeciesList list;
-    SpeciesList tmp;
+    SpeciesList tmp;           // scratch: the slots that leave, then the holes and the tail's survivors
     const ModelDev* model;
     Scalars* sc;
+    const uint32_t* dirty[2];  // the commit's dirty maps, by event parity
+    uint32_t g;                // event index (with g_base: its offset from *g_base)
+    const uint32_t* g_base;
 };
 
 // ---- launchers (psc_kernels.cu) ----
@@ -287,7 +292,8 @@ void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits
 void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
                           int blocks, cudaStream_t st);
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
-void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
+// the list's leavers' slots filled from its tail (one block)
+void launch_fill(const ReconcileArgs& r, cudaStream_t st);
 void launch_births(const EventArgs& a, cudaStream_t st);
 void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
 // molecule r (ids in species order, species s owning [offsets[s],
@@ -326,7 +332,7 @@ struct BatchLaunch {
 void launch_claim_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
 void launch_commit_batch(const EventArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
 void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
-void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st);
+void launch_fill_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
 void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st);
 
 // ---- radix sort (psc_sort.cu) ----

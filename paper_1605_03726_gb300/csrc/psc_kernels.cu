@@ -355,6 +355,13 @@ __device__ __forceinline__ bool won(const EventArgs& a, const Nb& nb, uint32_t i
     return false;
 }
 
+// the mirror word (4 x 4 x 2 brick) holding a voxel whose species changed:
+// the reconcile passes re-check only list entries in such bricks
+__device__ __forceinline__ void mark_dirty(uint32_t* dirty, uint32_t word)
+{
+    atomicOr(&dirty[word >> 5], 1u << (word & 31u));
+}
+
 // ---------------------------------------------------------------------------
 // claim
 // ---------------------------------------------------------------------------
@@ -464,6 +471,12 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
         for (uint32_t x = blk * blockDim.x + threadIdx.x; x < a.ct.clear_n; x += stride)
             a.ct.clear[x] = kEmptySlot;
     }
+    uint32_t* dirty = a.dirty[g & 1u];
+    if (GENERAL) {
+        // the previous event's map is read; empty it for the next one
+        uint32_t* old = a.dirty[(g & 1u) ^ 1u];
+        for (uint32_t x = blk * blockDim.x + threadIdx.x; x < a.dirty_words; x += stride) old[x] = 0u;
+    }
     for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
@@ -490,6 +503,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                         a.occ[v] = (uint16_t)(R.p0 + 1);
                         a.occ[nb.t] = (uint16_t)(R.p1 + 1);
                         bit_set(pb, bt);
+                        mark_dirty(dirty, bv.word);
                         const int slot = atomicAdd(&a.sc->births, 1);
                         if (slot < a.births_cap) {
                             Birth b;
@@ -509,6 +523,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                         a.occ[v] = 0;
                         bit_clear(a.bits, bv);
                     }
+                    mark_dirty(dirty, bv.word);
                     ++n_r1;
                 }
                 continue;
@@ -559,6 +574,8 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                 a.occ[nb.t] = (uint16_t)((straight ? R.p0 : R.p1) + 1);
                 a.occ[v] = (uint16_t)((straight ? R.p1 : R.p0) + 1);
             }
+            mark_dirty(dirty, bt.word);
+            mark_dirty(dirty, bv.word);
             ++n_r2;
         }
     }
@@ -898,7 +915,11 @@ cudaError_t launch_run(const RunArgs& r, int blocks, int threads, int per_thread
 // species y (a product that inherited this molecule's identity) moves to y's
 // list; one whose voxel is empty is dropped.  Species with reactions always
 // keep their codes in occ, and a vacant voxel never keeps the code of one, so
-// "occupied and code y + 1" identifies y exactly.
+// "occupied and code y + 1" identifies y exactly.  Only entries in bricks the
+// commit marked (a voxel there changed species) can have changed: the others
+// stay where they are without a look at the grid.  The entries that leave are
+// marked (voxel -1) and their slots noted; the fill pass then moves the
+// survivors from the end of the list into the slots below the new length.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int warp_alloc(int* counter, bool want)
 {
@@ -912,30 +933,35 @@ __device__ __forceinline__ int warp_alloc(int* counter, bool want)
     return want ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
-__device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, int blk, int nblk)
+__device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, uint32_t g, int blk, int nblk)
 {
     const int32_t n = r.sc->counts[r.x];
     const uint16_t self = (uint16_t)(r.x + 1);
+    const uint32_t* dirty = r.dirty[g & 1u];
+    int32_t* leave = r.tmp.vox;                          // slots of the entries that leave
     const int stride = nblk * blockDim.x;
     for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
-        const bool valid = idx < n;
-        int32_t v = 0; uint32_t id = 0; uint64_t img = 0; uint16_t o = 0;
-        if (valid) {
+        int32_t v = 0;
+        uint16_t o = 0;
+        bool leaving = false;
+        if (idx < n) {
             v = r.list.vox[idx];
-            id = r.list.ids[idx];
-            img = r.list.img[idx];
             int32_t i, j, k;
             decode(r.geo, (uint32_t)v, i, j, k);
-            o = occupied(r.bits, bitpos(r.geo, i, j, k)) ? r.occ[v] : (uint16_t)0;
+            const BitPos bp = bitpos(r.geo, i, j, k);
+            if ((dirty[bp.word >> 5] >> (bp.word & 31u)) & 1u) {
+                o = occupied(r.bits, bp) ? r.occ[v] : (uint16_t)0;
+                leaving = o != self;
+            }
         }
-        const bool keep = valid && o == self;
-        const int slot = warp_alloc(&r.sc->tmp_count[r.x], keep);
-        if (keep) {
-            r.tmp.vox[slot] = v;
-            r.tmp.ids[slot] = id;
-            r.tmp.img[slot] = img;
-        } else if (valid && o != 0 && o != kBlocked) {
+        const int slot = warp_alloc(&r.sc->tmp_count[r.x], leaving);
+        if (!leaving) continue;
+        leave[slot] = idx;
+        const uint32_t id = r.list.ids[idx];
+        const uint64_t img = r.list.img[idx];
+        r.list.vox[idx] = -1;
+        if (o != 0 && o != kBlocked) {
             const int y = o - 1;
             const SpeciesList dst = r.model->lists[y];
             const int s2 = atomicAdd(&r.sc->counts[y], 1);
@@ -950,26 +976,56 @@ __device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, int blk, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
+__device__ __forceinline__ uint32_t reconcile_event(const ReconcileArgs& r)
 {
-    reconcile_body(r, blockIdx.x, gridDim.x);
+    return r.g_base ? __ldcg(r.g_base) + r.g : r.g;
 }
 
-__device__ __forceinline__ void copyback_body(const ReconcileArgs& r, int blk, int nblk)
+__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
 {
-    const int32_t m = r.sc->tmp_count[r.x];
-    if (blk == 0 && threadIdx.x == 0) r.sc->counts[r.x] = m;
-    const int stride = nblk * blockDim.x;
-    for (int idx = blk * blockDim.x + threadIdx.x; idx < m; idx += stride) {
-        r.list.vox[idx] = r.tmp.vox[idx];
-        r.list.ids[idx] = r.tmp.ids[idx];
-        r.list.img[idx] = r.tmp.img[idx];
+    reconcile_body(r, reconcile_event(r), blockIdx.x, gridDim.x);
+}
+
+// One block: k entries left; the new length is n - k.  Every slot below it
+// that an entry left (a hole) takes one of the surviving entries at or above
+// it (there are as many); entries that left above it are simply cut off.
+__device__ __forceinline__ void fill_body(const ReconcileArgs& r)
+{
+    __shared__ int s_h, s_s;
+    const int32_t n = r.sc->counts[r.x];
+    const int32_t k = min(r.sc->tmp_count[r.x], n);
+    if (k <= 0) return;
+    const int32_t n2 = n - k;
+    int32_t* holes = reinterpret_cast<int32_t*>(r.tmp.ids);
+    int32_t* surv = reinterpret_cast<int32_t*>(r.tmp.img);
+    if (threadIdx.x == 0) {
+        s_h = 0;
+        s_s = 0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        const int32_t h = r.tmp.vox[q];
+        if (h < n2) holes[atomicAdd(&s_h, 1)] = h;
+    }
+    for (int p = n2 + threadIdx.x; p < n; p += blockDim.x)
+        if (r.list.vox[p] >= 0) surv[atomicAdd(&s_s, 1)] = p;
+    __syncthreads();
+    const int m = min(s_h, s_s);
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const int32_t h = holes[q], p = surv[q];
+        r.list.vox[h] = r.list.vox[p];
+        r.list.ids[h] = r.list.ids[p];
+        r.list.img[h] = r.list.img[p];
+    }
+    if (threadIdx.x == 0) {
+        r.sc->counts[r.x] = n2;
+        if (s_h != s_s) atomicOr(&r.sc->err, kErrListOverflow);
     }
 }
 
-__global__ void __launch_bounds__(256) k_copyback(const ReconcileArgs r)
+__global__ void __launch_bounds__(1024) k_fill(const ReconcileArgs r)
 {
-    copyback_body(r, blockIdx.x, gridDim.x);
+    fill_body(r);
 }
 
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
@@ -977,9 +1033,9 @@ void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStrea
     k_reconcile<<<blocks, threads, 0, st>>>(r);
 }
 
-void launch_copyback(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
+void launch_fill(const ReconcileArgs& r, cudaStream_t st)
 {
-    k_copyback<<<blocks, threads, 0, st>>>(r);
+    k_fill<<<1, 1024, 0, st>>>(r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1369,15 +1425,15 @@ __global__ void __launch_bounds__(256) k_reconcile_batch(const ReconcileArgs* tm
     int nblk;
     const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
     const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
-    reconcile_body(r, blockIdx.x - I.block0, nblk);
+    reconcile_body(r, I.g, blockIdx.x - I.block0, nblk);
 }
 
-__global__ void __launch_bounds__(256) k_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch bl)
+// one block per item
+__global__ void __launch_bounds__(1024) k_fill_batch(const ReconcileArgs* tmpl, const BatchLaunch bl)
 {
-    int nblk;
-    const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
+    const BatchItem I = bl.item[blockIdx.x];
     const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
-    copyback_body(r, blockIdx.x - I.block0, nblk);
+    fill_body(r);
 }
 
 // one block per item
@@ -1403,9 +1459,9 @@ void launch_reconcile_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, in
     k_reconcile_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
 }
 
-void launch_copyback_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, int threads, cudaStream_t st)
+void launch_fill_batch(const ReconcileArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)
 {
-    k_copyback_batch<<<bl.total_blocks, threads, 0, st>>>(tmpl, bl);
+    k_fill_batch<<<bl.n, 1024, 0, st>>>(tmpl, bl);
 }
 
 void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStream_t st)

@@ -61,6 +61,8 @@ struct psc_lattice {
     ModelDev* model_d = nullptr;
     uint16_t* occ = nullptr;
     uint32_t* bits = nullptr;          // vacancy mirrors, one bit per voxel, one mirror per compartment
+    uint32_t* dirty[2] = {nullptr, nullptr};   // by event parity: mirror words whose voxels changed species
+    uint32_t dirty_words = 0;
     uint64_t mirror_n = 0;             // words of one mirror
     int32_t ncomp = 1;                 // compartments (Sec. 2)
     std::vector<uint8_t> labels;       // compartment of every voxel (empty: all 0)

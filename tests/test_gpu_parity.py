@@ -349,3 +349,29 @@ def test_tile_kernel_above_molecule_list_capacity():
         else:
             assert kt["tile_events"] == 0 and kt["claim_launches"] == 6
         g.close()
+
+
+@pytest.mark.parametrize("claim_table", [1, 2])
+def test_many_reactions_per_event(claim_table):
+    # A + B -> C with p_AB clamped to 1 and A + C -> D, both at 20 % on a ragged
+    # periodic lattice: thousands of molecules react in every early event, so
+    # the list upkeep has thousands of leavers and holes to fill per event
+    shape = (46, 44, 40)
+    V = shape[0] * shape[1] * shape[2]
+
+    def recipe(L):
+        a = L.add_species(2e-12, int(0.2 * V))
+        b = L.add_species(1e-12, int(0.2 * V))
+        c = L.add_species(0.5e-12, 0)
+        d = L.add_species(0.0, 0)
+        L.add_reaction([a, b], [c], 1e-17)
+        L.add_reaction([a, c], [d], 1e-17)
+        L.add_reaction([c], [a, b], 50.0)
+
+    g, o = build_both(shape, recipe, 29, claim_table=claim_table)
+    for chunk in (1, 2, 5, 20):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+    st = o.stats()
+    assert st["reactions2"] > 10000

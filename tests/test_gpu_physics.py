@@ -102,3 +102,35 @@ def test_fcc_long_run_properties():
     assert set(np.unique(d).tolist()) <= {0, 12}
     assert int(np.count_nonzero(d)) == L.stats()["hops"] - h0
     L.close()
+
+
+def test_cell_long_run_properties():
+    # 256^3 lattice holding a round cell (cytoplasm 35 % of the voxels); 2^20
+    # walkers confined to the cytoplasm, 1000 events under the automatic
+    # kernel choice: exclusion, ids kept, every molecule still in the
+    # cytoplasm, and one more event moves each by 0 or one voxel diameter
+    import models
+    shape = (256, 256, 256)
+    lab = models.cell_labels(*shape, radius=200.0)
+    n = 1 << 20
+    L = psc.Lattice(*shape, voxel_radius=RV)
+    L.set_compartments(lab, 3)
+    s = L.add_species(D, n, compartment=2)
+    L.set_options(collect_stats=1)
+    L.populate(5)
+    _, id0 = L.unwrapped(s)
+    L.run_events(1000)
+    ijk, ids = L.coords(s)
+    assert np.array_equal(ids, id0)
+    v = ijk[:, 0].astype(np.int64) + 256 * (ijk[:, 1] + 256 * ijk[:, 2].astype(np.int64))
+    assert np.unique(v).size == n
+    assert (lab[v] == 2).all()
+    assert int(np.count_nonzero(L.grid())) == n
+    x1, _ = L.unwrapped(s)
+    h0 = L.stats()["hops"]
+    L.run_events(1)
+    x2, _ = L.unwrapped(s)
+    d = axes3(x1, x2).sum(axis=1)
+    assert set(np.unique(d).tolist()) <= {0, 12}
+    assert int(np.count_nonzero(d)) == L.stats()["hops"] - h0
+    L.close()

@@ -154,3 +154,29 @@ def test_allocation_failures_are_reported_and_cleaned_up():
     L.run_events(2)
     L.synchronize()
     L.close()
+
+
+def test_subvolume_barrier_wait_runs_out_and_is_reported():
+    # the sub-volume rule's persistent launch waits at bounded grid barriers too
+    shape = (48, 48, 48)
+    L = psc.Lattice(*shape, voxel_radius=1e-8)
+    L.set_options(subvolume=1, barrier_timeout_us=20000, barrier_phantom=1)
+    _walkers(L)
+    t0 = time.monotonic()
+    L.run_events(4)
+    with pytest.raises(psc.EngineError) as err:
+        L.synchronize()
+    assert err.value.rc == psc.E_TIMEOUT
+    assert time.monotonic() - t0 < 10.0
+    L.close()
+    G = psc.Lattice(*shape, voxel_radius=1e-8)
+    G.set_options(subvolume=1)
+    s = _walkers(G)
+    G.run_events(6)
+    o = oracle.Lattice(*shape, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SUBVOL)
+    o.add_species(D, N)
+    o.populate(17)
+    o.run_events(6)
+    a, b = G.coords(s), o.coords(s)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    G.close()

@@ -1521,13 +1521,13 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
     if (!L || !o) return PSC_E_ARG;
     if (o->block_threads && (o->block_threads < 32 || o->block_threads > 256 || (o->block_threads & 31)))
         return PSC_E_ARG;
-    if (o->blocks_per_sm < 0 || o->graph_events < 0) return PSC_E_ARG;
+    if (o->blocks_per_sm < 0) return PSC_E_ARG;
     graph_cache_clear(L);                            // captured launches follow the options
     if (o->resort_period) L->opt.resort_period = o->resort_period;
     if (o->block_threads) L->opt.block_threads = o->block_threads;
     if (o->blocks_per_sm) L->opt.blocks_per_sm = o->blocks_per_sm;
     if (o->collect_stats) L->opt.collect_stats = o->collect_stats;
-    if (o->graph_events) L->opt.graph_events = o->graph_events;
+    if (o->graph_events) L->opt.graph_events = o->graph_events < 0 ? 0 : o->graph_events;
     if (o->time_kernels) L->opt.time_kernels = o->time_kernels;
     if (o->claim_table) {
         if (o->claim_table < -1 || o->claim_table > 2) return PSC_E_ARG;

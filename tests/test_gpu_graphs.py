@@ -1,7 +1,8 @@
-"""Per-event runs replayed from CUDA graphs (psc_options.graph_events) give
-the same lattice as ordinary launches and as the oracle, whatever the run
-length, the claim tables, the re-sort period or the species mix; options set
-between runs drop the captured graphs; with kernel timing on, graphs stay off.
+"""Per-event runs replayed from CUDA graphs (psc_options.graph_events, on by
+default) give the same lattice as ordinary launches (graph_events = -1) and as
+the oracle, whatever the run length, the claim tables, the re-sort period or
+the species mix; options set between runs drop the captured graphs; with
+kernel timing on, graphs stay off.
 """
 import numpy as np
 import pytest
@@ -42,7 +43,7 @@ def test_graph_replay_matches_ordinary_launches_and_oracle(name, shape, bnd, rec
     runs = {}
     for graphs in (0, k):
         L = psc.Lattice(*shape, voxel_radius=1e-8, boundary=bnd)
-        L.set_options(claim_table=claim_table, resort_period=24, **({"graph_events": graphs} if graphs else {}))
+        L.set_options(claim_table=claim_table, resort_period=24, graph_events=graphs or -1)
         recipe(L)
         L.populate(6)
         for chunk in (5, 200, 333):
@@ -69,6 +70,7 @@ def test_graphs_replay_and_follow_option_changes():
         models.reaction_diffusion_ab(M, 2000, 2000)
         M.populate(2)
     L.set_options(graph_events=32)
+    U.set_options(graph_events=-1)                   # ordinary launches
     L.run(0.02)
     U.run(0.02)
     same(state(L, 3), state(U, 3), "run to t")
@@ -102,7 +104,7 @@ def test_graph_replay_with_compartments_and_fcc():
         runs = {}
         for graphs in (0, 16):
             L = psc.Lattice(*shape, voxel_radius=1e-8, boundary=bnd)
-            L.set_options(resort_period=16, **({"graph_events": graphs} if graphs else {}))
+            L.set_options(resort_period=16, graph_events=graphs or -1)
             models.receptor_binding(L, lab, 1200, 500, n_x=300, n_outside=1000, koff=2e3)
             L.populate(3)
             L.run_events(40)

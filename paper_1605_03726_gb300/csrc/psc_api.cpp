@@ -130,6 +130,9 @@ EventArgs event_args(const psc_lattice* L, int s)
     a.dirty[0] = L->dirty[0];
     a.dirty[1] = L->dirty[1];
     a.dirty_words = L->dirty_words;
+    // the claim outcomes live in the scratch list between claim and commit
+    // (its capacity is the largest list's; the list passes that use it come after)
+    a.dec = reinterpret_cast<uint8_t*>(L->tmp.vox);
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;

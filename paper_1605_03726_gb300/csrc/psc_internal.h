@@ -148,10 +148,17 @@ struct EventArgs {
     const uint32_t* g_base;    // null, or the device word holding the index a replayed graph starts at
     uint32_t* dirty[2];        // by event parity: a bit per mirror word whose voxels changed species
     uint32_t dirty_words;      // words of one dirty map
+    uint8_t* dec;              // null, or per list entry the claim's outcome for the commit (kDec*)
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;
 };
+
+// Outcome of a molecule's claim phase, kept for its commit phase: the
+// direction 0-11 of the voxel it claimed, no claim, or a first-order firing
+// (the commit redraws those)
+constexpr uint8_t kDecNone = 12;
+constexpr uint8_t kDecFire = 13;
 
 // A stretch of consecutive events of one species without reactions, run by
 // one persistent cooperative launch.

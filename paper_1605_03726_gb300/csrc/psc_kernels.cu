@@ -385,10 +385,12 @@ __device__ __forceinline__ void claim_body(const EventArgs& a, uint32_t g, int b
         uint32_t u[4];
         philox(id, g, c2, 0u, a.key0, a.key1, u);
         ++n_att;
+        uint8_t out = kDecNone;
         if (GENERAL) {
             const ModelDev* M = a.model;
             if (M->n_fo[a.s] > 0 && (uint64_t)u[2] < M->T_fire[a.s]) {
                 ++n_fire;
+                if (a.dec) a.dec[idx] = kDecFire;
                 const int r = pick_first_order(M, a.s, u[3]);
                 if (M->rx[r].np == 2) {
                     // second product: uniform pick among neighbours vacant now
@@ -415,22 +417,26 @@ __device__ __forceinline__ void claim_body(const EventArgs& a, uint32_t g, int b
         }
         const int d = (int)__umulhi(u[0], 12u);
         Nb nb;
-        if (!neighbor(a.geo, i, j, k, d, nb)) continue;
-        if (!occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) {
-            claim<HASH>(a, nb, id);
-        } else if (GENERAL) {
-            const uint16_t o = a.occ[nb.t];
-            if (o != 0 && o != kBlocked) {
-                const int r = a.model->pair[a.s][o - 1];
-                if (r >= 0) {
-                    ++n_col;
-                    if ((uint64_t)u[1] < a.model->rx[r].T) {
-                        ++n_acc;
-                        claim<HASH>(a, nb, id);
+        if (neighbor(a.geo, i, j, k, d, nb)) {
+            if (!occupied(a.bits, bitpos(a.geo, nb.i, nb.j, nb.k))) {
+                claim<HASH>(a, nb, id);
+                out = (uint8_t)d;
+            } else if (GENERAL) {
+                const uint16_t o = a.occ[nb.t];
+                if (o != 0 && o != kBlocked) {
+                    const int r = a.model->pair[a.s][o - 1];
+                    if (r >= 0) {
+                        ++n_col;
+                        if ((uint64_t)u[1] < a.model->rx[r].T) {
+                            ++n_acc;
+                            claim<HASH>(a, nb, id);
+                            out = (uint8_t)d;
+                        }
                     }
                 }
             }
         }
+        if (a.dec) a.dec[idx] = out;
     }
     if (a.collect_stats) {
         flush_stat(&a.sc->stats[kStatAttempts], n_att);
@@ -480,14 +486,19 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
     for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
         if (idx >= n) continue;
+        // the claim phase's outcome: a molecule that claimed nothing cannot
+        // have won anything; one that claimed knows its direction without a
+        // second draw; only first-order firings are drawn again
+        const int known = a.dec ? (int)a.dec[idx] : (int)kDecFire;
+        if (known == kDecNone) continue;
         const uint32_t v = (uint32_t)a.list.vox[idx];
         const uint32_t id = a.list.ids[idx];
         int32_t i, j, k;
         decode(a.geo, v, i, j, k);
         const BitPos bv = bitpos(a.geo, i, j, k);
-        uint32_t u[4];
-        philox(id, g, c2, 0u, a.key0, a.key1, u);
-        if (GENERAL) {
+        uint32_t u[4] = {0u, 0u, 0u, 0u};
+        if (known == kDecFire) philox(id, g, c2, 0u, a.key0, a.key1, u);
+        if (GENERAL && known == kDecFire) {
             const ModelDev* M = a.model;
             if (M->n_fo[a.s] > 0 && (uint64_t)u[2] < M->T_fire[a.s]) {
                 const ReactionDev R = M->rx[pick_first_order(M, a.s, u[3])];
@@ -529,7 +540,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                 continue;
             }
         }
-        const int d = (int)__umulhi(u[0], 12u);
+        const int d = known == kDecFire ? (int)__umulhi(u[0], 12u) : known;
         Nb nb;
         if (!neighbor(a.geo, i, j, k, d, nb)) continue;
         if (!won<HASH>(a, nb, id)) continue;                   // lost, or never claimed

@@ -129,7 +129,10 @@ typedef struct {
                                  counters) comes up and replayed from then
                                  on, the event index read from device memory;
                                  same results, fewer launches.  Off while
-                                 time_kernels is on; -1 = off (default 32)     */
+                                 time_kernels is on; -1 = off (default 32).
+                                 A capture takes in everything queued on the
+                                 lattice's stream meanwhile: a stream that
+                                 other threads also feed needs -1              */
     int32_t time_kernels;     /* 1 = record CUDA events around the kernels of
                                  every event (psc_kernel_times_get), -1 off     */
     int32_t claim_table;      /* before populate: 1 = one claim word per voxel,

@@ -515,6 +515,58 @@ def serving_arm(args, local):
     }
 
 
+# the serving workload on the oracle, one replica per host core
+SERVE_EVENTS = 2 * 2000                    # A and B, 2000 hop intervals each (equal tau)
+
+
+def _serve_oracle_task(task):
+    """One replica on the oracle, from its placement until its last event or the
+    deadline (wall clock), whichever comes first: (events done, events, attempts)."""
+    q, deadline = task
+    if time.time() >= deadline:
+        return 0, SERVE_EVENTS, 0
+    import oracle
+    L = oracle.Lattice(*q["shape"], SERVE_RV, oracle.PERIODIC_ALL, oracle.RULE_SYNC)
+    L.add_species(SERVE_D, q["counts"][0])
+    L.add_species(SERVE_D, q["counts"][1])
+    L.add_species(0.0, 0)
+    L.add_reaction([0, 1], [2], SERVE_K)
+    L.populate(q["seed"])
+    chunk = max(1, min(200, 300000 // max(1, q["counts"][0] + q["counts"][1])))
+    done = 0
+    while done < SERVE_EVENTS and time.time() < deadline:
+        n = min(chunk, SERVE_EVENTS - done)
+        L.run_events(n)
+        done += n
+    attempts = L.stats()["attempts"]
+    L.close()
+    return done, SERVE_EVENTS, attempts
+
+
+def serving_cpu_baseline(seconds, reps, cores=None):
+    """The replicas of the serving workload on the oracle, in workload order, one
+    per host core at a time (a spawned process per core), for a bounded wall time.
+    A replica that ends counts as one, one cut off at the deadline by the share
+    of its events it ran."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")                  # never fork a process that has used the GPU
+    with ctx.Pool(cores) as pool:
+        pool.map(_serve_oracle_task, [(reps[0], 0.0)] * cores)       # start the workers
+        t0 = time.time()
+        tasks = [(q, t0 + seconds) for q in reps]
+        res = list(pool.imap(_serve_oracle_task, tasks))
+        dt = time.time() - t0
+    whole = sum(1 for d, n, _ in res if d == n)
+    share = sum(d / n for d, n, _ in res)
+    return {"value": round(share / dt, 4), "unit": "replicas/s", "cores": cores, "kind": "oracle",
+            "attempts_per_s": round(sum(a for _, _, a in res) / dt, 1),
+            "sample": "the workload's replicas in order, one per process on %d cores of %s, for %.1f s of wall "
+                      "clock (placement included): %d ended, %.2f replica-equivalents in all (a replica cut off "
+                      "counts by the share of its %d events it ran)" % (cores, cpu_model(), dt, whole, share,
+                                                                         SERVE_EVENTS)}
+
+
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -619,6 +671,9 @@ def main():
         out["e2e"] = res["e2e"]
     if world == 1 and not args.no_serving:
         out["serving"] = serving_arm(args, local)
+        if not args.no_cpu_baseline:
+            out["serving"]["cpu_baseline"] = serving_cpu_baseline(args.cpu_seconds,
+                                                                  serving_replicas(args.replicas))
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args)
     print(json.dumps(out))

@@ -549,6 +549,9 @@ def serving_cpu_baseline(seconds, reps, cores=None):
     A replica that ends counts as one, one cut off at the deadline by the share
     of its events it ran."""
     import multiprocessing as mp
+
+    import oracle
+    oracle.lib()                                   # built once here, not by every worker
     cores = cores or os.cpu_count() or 1
     ctx = mp.get_context("spawn")                  # never fork a process that has used the GPU
     with ctx.Pool(cores) as pool:

@@ -46,3 +46,53 @@ def test_library_is_built_for_sm_103a():
     from paper_1605_03726_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
     assert os.path.exists(build.LIB)
+
+
+def test_null_handles_and_outputs_are_rejected():
+    # every entry point checks its handle and output pointers before it
+    # touches the device, so these run without a GPU
+    import ctypes
+    L = psc.lib()
+    E = psc.E_ARG
+    i32, i64, u32, dbl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_uint32(), ctypes.c_double()
+    assert L.psc_add_species(None, 1e-12, 10, ctypes.byref(i32)) == E
+    r2 = (ctypes.c_int32 * 2)(0, 1)
+    assert L.psc_add_reaction(None, r2, 2, r2, 1, 1e-19, ctypes.byref(i32)) == E
+    assert L.psc_set_compartments(None, None, 2) == E
+    assert L.psc_species_compartment(None, 0, 0) == E
+    assert L.psc_populate(None, 1) == E
+    assert L.psc_run(None, 1.0) == E and L.psc_run_events(None, 1) == E
+    assert L.psc_synchronize(None) == E
+    assert L.psc_counts(None, None, 1) == E
+    assert L.psc_coords(None, 0, None, None, 0, ctypes.byref(i64)) == E
+    assert L.psc_unwrapped(None, 0, None, None, 0, ctypes.byref(i64)) == E
+    assert L.psc_grid(None, None) == E
+    assert L.psc_time(None, ctypes.byref(dbl)) == E
+    assert L.psc_event_index(None, ctypes.byref(u32)) == E
+    assert L.psc_stats_get(None, None) == E
+    assert L.psc_set_options(None, None) == E
+    assert L.psc_kernel_times_get(None, None) == E
+    assert L.psc_autotune(None, 10, None) == E
+    assert L.psc_device_bytes(None, ctypes.byref(i64)) == E
+    assert L.psc_tau(None, 0) == 0.0 and L.psc_p_ab(None, 0) == 0.0
+    L.psc_lattice_destroy(None)
+    # batches and the server
+    assert L.psc_batch_create(None, 0, None) == E
+    h = ctypes.c_void_p()
+    assert L.psc_batch_create(ctypes.byref(h), -1, None) == E
+    assert L.psc_batch_add(None, None) == E and L.psc_batch_remove(None, None) == E
+    assert L.psc_batch_size(None, ctypes.byref(i32)) == E
+    assert L.psc_batch_run_events(None, 1) == E and L.psc_batch_run(None, 1.0) == E
+    assert L.psc_batch_autotune(None, 10, None) == E
+    assert L.psc_batch_launches(None) == 0
+    L.psc_batch_destroy(None)
+    assert L.psc_server_create(None, 0, None, 1 << 20, 1) == E
+    assert L.psc_server_create(ctypes.byref(h), 0, None, 0, 1) == E
+    assert L.psc_server_create(ctypes.byref(h), 0, None, 1 << 20, 0) == E
+    assert L.psc_server_submit(None, None, ctypes.byref(i64)) == E
+    assert L.psc_server_step(None, 1, ctypes.byref(i32), ctypes.byref(i32)) == E
+    assert L.psc_server_result(None, 0, None, 0, ctypes.byref(dbl)) == E
+    assert L.psc_server_memory(None, ctypes.byref(i64), ctypes.byref(i64)) == E
+    L.psc_server_destroy(None)
+    # the allocation-free stepper checks its buffers and shape first
+    assert L.psc_hop_events_static(8, 8, 8, 7, 1, 0, 0, 1, None, None, None, 1, None) == E

@@ -12,6 +12,10 @@ order per event, sequential within a colour).
                   (12 x 12 directions x which colour goes first, each order
                   with probability 1/2) against seeded runs (chi-square)
   physics         MSD = 6 D t for isolated walkers
+
+The special case, the once-per-event check and MSD also run on FCC lattices
+(App. B): the colouring only needs every neighbour within one voxel on each
+axis, which holds for both stackings.
 """
 import collections
 import itertools
@@ -38,10 +42,11 @@ def same(a, b):
         assert np.array_equal(x, u) and np.array_equal(y, v)
 
 
-def test_one_subvolume_is_the_sequential_rule():
+@pytest.mark.parametrize("kind", [0, oracle.FCC])
+def test_one_subvolume_is_the_sequential_rule(kind):
     lat = {}
     for rule in (oracle.RULE_SUBVOL, oracle.RULE_SEQ_ID):
-        L = oracle.Lattice(2, 2, 2, 1e-8, 0, rule)
+        L = oracle.Lattice(2, 2, 2, 1e-8, kind, rule)
         a = L.add_species(1e-12, 2)
         b = L.add_species(1e-12, 2)
         c = L.add_species(0.5e-12, 0)
@@ -71,8 +76,9 @@ def test_walkers_that_never_meet_move_the_same_under_every_rule():
         assert np.array_equal(i, i0) and np.array_equal(x, x0), rule
 
 
-def test_no_molecule_moves_twice_in_one_event():
-    L = oracle.Lattice(24, 24, 24, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SUBVOL)
+@pytest.mark.parametrize("kind", [0, oracle.FCC])
+def test_no_molecule_moves_twice_in_one_event(kind):
+    L = oracle.Lattice(24, 24, 24, 1e-8, oracle.PERIODIC_ALL | kind, oracle.RULE_SUBVOL)
     s = L.add_species(1e-12, int(0.3 * 24 ** 3))
     L.populate(2)
     before, _ = L.unwrapped(s)
@@ -152,9 +158,11 @@ def test_subvol_needs_periods_that_keep_the_colours():
     oracle.Lattice(7, 5, 3, 1e-8, 0, oracle.RULE_SUBVOL).close()
 
 
-def test_subvol_msd_equals_6Dt(golden):
+@pytest.mark.parametrize("kind", [0, oracle.FCC])
+def test_subvol_msd_equals_6Dt(golden, kind):
     rv, D, n_events = 5e-9, 10e-12, 48
-    L = oracle.Lattice(128, 128, 128, rv, oracle.PERIODIC_ALL, oracle.RULE_SUBVOL)
+    nk = 120 if kind else 128                 # FCC: periodic k a multiple of 3 (and of 4)
+    L = oracle.Lattice(128, 128, nk, rv, oracle.PERIODIC_ALL | kind, oracle.RULE_SUBVOL)
     s = L.add_species(D, 20000)
     L.populate(4)
     x0, _ = L.unwrapped(s)

@@ -32,44 +32,49 @@ class Stats(ctypes.Structure):
         return d
 
 
+def load(path):
+    """Open an oracle shared library at `path` and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64, u32, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "psco_lattice_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, i32, dbl, u32, i32]),
+        "psco_add_species": (ctypes.c_int, [P, dbl, i64, ctypes.POINTER(i32)]),
+        "psco_add_reaction": (ctypes.c_int, [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32, dbl, ctypes.POINTER(i32)]),
+        "psco_set_compartments": (ctypes.c_int, [P, P, i32]),
+        "psco_species_compartment": (ctypes.c_int, [P, i32, i32]),
+        "psco_populate": (ctypes.c_int, [P, u64]),
+        "psco_run": (ctypes.c_int, [P, dbl]),
+        "psco_run_events": (ctypes.c_int, [P, i64]),
+        "psco_counts": (ctypes.c_int, [P, P, i32]),
+        "psco_coords": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
+        "psco_unwrapped": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
+        "psco_grid": (ctypes.c_int, [P, P]),
+        "psco_time": (ctypes.c_int, [P, ctypes.POINTER(dbl)]),
+        "psco_event_index": (ctypes.c_int, [P, ctypes.POINTER(u32)]),
+        "psco_stats_get": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
+        "psco_check": (ctypes.c_int, [P]),
+        "psco_place": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(u32)]),
+        "psco_lattice_destroy": (None, [P]),
+        "psco_tau": (dbl, [P, i32]),
+        "psco_p_ab": (dbl, [P, i32]),
+        "psco_threshold": (u64, [dbl]),
+        "psco_philox4x32_10": (None, [P, P, P]),
+        "psco_neighbor": (ctypes.c_int, [P, i32, i32, i32, i32, P, P]),
+        "psco_center": (None, [i32, i32, i32, P]),
+        "psco_center_fcc": (None, [i32, i32, i32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(_build())
-        P = ctypes.c_void_p
-        i32, i64, u32, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
-        sig = {
-            "psco_lattice_create": (ctypes.c_int, [ctypes.POINTER(P), i32, i32, i32, dbl, u32, i32]),
-            "psco_add_species": (ctypes.c_int, [P, dbl, i64, ctypes.POINTER(i32)]),
-            "psco_add_reaction": (ctypes.c_int, [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), i32, dbl, ctypes.POINTER(i32)]),
-            "psco_set_compartments": (ctypes.c_int, [P, P, i32]),
-            "psco_species_compartment": (ctypes.c_int, [P, i32, i32]),
-            "psco_populate": (ctypes.c_int, [P, u64]),
-            "psco_run": (ctypes.c_int, [P, dbl]),
-            "psco_run_events": (ctypes.c_int, [P, i64]),
-            "psco_counts": (ctypes.c_int, [P, P, i32]),
-            "psco_coords": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
-            "psco_unwrapped": (ctypes.c_int, [P, i32, P, P, i64, ctypes.POINTER(i64)]),
-            "psco_grid": (ctypes.c_int, [P, P]),
-            "psco_time": (ctypes.c_int, [P, ctypes.POINTER(dbl)]),
-            "psco_event_index": (ctypes.c_int, [P, ctypes.POINTER(u32)]),
-            "psco_stats_get": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
-            "psco_check": (ctypes.c_int, [P]),
-            "psco_place": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(u32)]),
-            "psco_lattice_destroy": (None, [P]),
-            "psco_tau": (dbl, [P, i32]),
-            "psco_p_ab": (dbl, [P, i32]),
-            "psco_threshold": (u64, [dbl]),
-            "psco_philox4x32_10": (None, [P, P, P]),
-            "psco_neighbor": (ctypes.c_int, [P, i32, i32, i32, i32, P, P]),
-            "psco_center": (None, [i32, i32, i32, P]),
-            "psco_center_fcc": (None, [i32, i32, i32, P]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = load(_build())
     return _lib
 
 

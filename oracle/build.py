@@ -18,12 +18,18 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in SOURCES + [os.path.join(HERE, "psco.h")])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    return compile_library(SOURCES, LIB)
+
+
+def compile_library(sources, out):
+    """Compile C sources into the shared library `out` with the oracle's flags
+    (also used by tests that build a copy of the oracle with a planted mistake)."""
+    tmp = out + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-Wall", "-Wextra", "-o", tmp] + SOURCES + ["-lm"]
+           "-Wall", "-Wextra", "-o", tmp] + list(sources) + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -71,19 +71,25 @@ class Model:
 
 
 def options(model, grid, s, v):
-    """Choices of one molecule of species s at voxel v given `grid` (voxel -> species)."""
+    """Choices of one molecule of species s at voxel v given `grid` (voxel -> species).
+
+    First order (Sec. 2.4.1): the molecule fires with probability pf; Eq. 5
+    then takes reaction u with probability a_u / a_0 = k_u / sum(k), in the
+    order the reactions were registered."""
     out = []
     pf = model.fire.get(s, 0.0)
     if pf > 0.0:
-        (prods, _), = model.fo[s]          # one first-order reaction in these tests
-        if len(prods) == 2:
-            vac = [t for t in model.nbr[v] if t is not None and t not in grid]
-            if vac:
-                out += [(("fire2", t), pf / len(vac)) for t in vac]
+        ktot = sum(k for _, k in model.fo[s])
+        for u, (prods, k) in enumerate(model.fo[s]):
+            pu = pf * k / ktot
+            if len(prods) == 2:
+                vac = [t for t in model.nbr[v] if t is not None and t not in grid]
+                if vac:
+                    out += [(("fire2", t, u), pu / len(vac)) for t in vac]
+                else:
+                    out.append((("none",), pu))
             else:
-                out.append((("none",), pf))
-        else:
-            out.append((("fire1",), pf))
+                out.append((("fire1", u), pu))
     for d in range(12):
         t = model.nbr[v][d]
         w = (1.0 - pf) / 12.0
@@ -118,12 +124,12 @@ def apply_action(model, grid, s, v, act, births):
         if len(prods) == 2:
             grid[v] = (prods[1], sid)            # second product: mover's voxel and id
     elif kind == "fire1":
-        (prods, _), = model.fo[s]
+        prods, _ = model.fo[s][act[1]]
         del grid[v]
         if prods:
             grid[v] = (prods[0], sid)
     elif kind == "fire2":
-        (prods, _), = model.fo[s]
+        prods, _ = model.fo[s][act[2]]
         grid[v] = (prods[0], sid)
         births.append((sid, act[1], prods[1]))
 
@@ -311,3 +317,106 @@ def test_random_order_rule():
     state = [(0, 0, a), (1, 0, m.nbr[a][0])]
     exact = exact_seq(m, state, 0, 2, orders=[(0, 1), (1, 0)])
     compare(exact, simulate(m, state, oracle.RULE_SEQ_RANDOM, TRIALS), TRIALS)
+
+
+# --------------------------------------------------------------------------
+# Eq. 5: the choice among several first-order reactions of one species
+# --------------------------------------------------------------------------
+# Sec. 2.4.1: once a molecule fires, the u-th of its first-order reactions is
+# taken with probability a_u / a_0 (Eq. 5), a_u the propensity of reaction u.
+# Per molecule a_u / a_0 = k_u / sum(k).  The pins below take those shares
+# from the rate constants alone; the oracle draws the choice with u3 against
+# integer cut points.  Planted mistakes (reversed cut points, the choice drawn
+# from u2, cut points that do not accumulate) must each fail them.
+
+# in-place conversions A -> B, A -> C, A -> D with shares 2/15, 4/15, 9/15;
+# sum(k) tau = 0.5 at D = 1 um^2/s and r_v = 10 nm
+THREE_WAY = [((0,), (1,), 1000.0), ((0,), (2,), 2000.0), ((0,), (3,), 4500.0)]
+
+PLANTS = {
+    "reversed cut points": ("if ((uint64_t)u3 < S->cum[u]) return S->fo[u];",
+                            "if ((uint64_t)u3 < S->cum[u]) return S->fo[S->n_fo - 1 - u];"),
+    "choice drawn from u2": ("int32_t r = pick_first_order(S, u[3]);",
+                             "int32_t r = pick_first_order(S, u[2]);"),
+    "cut points not cumulative": ("psco_threshold(ktot > 0.0 ? cum / ktot : 1.0)",
+                                  "psco_threshold(ktot > 0.0 ? L->rx[S->fo[u]].k / ktot : 1.0)"),
+}
+
+
+def branching_counts(reactions, seeds=(11, 12), n_a=30000, dims=(64, 64, 64)):
+    """Fires and products of one event of n_a molecules of A (the only mobile
+    species) that convert in place; products of reaction u are species u + 1."""
+    fires, made = 0, np.zeros(len(reactions), dtype=np.int64)
+    for seed in seeds:
+        L = oracle.Lattice(*dims, 1e-8, oracle.PERIODIC_ALL)
+        L.add_species(1e-12, n_a)
+        for _ in reactions:
+            L.add_species(0.0, 0)
+        for re, pr, k in reactions:
+            L.add_reaction(re, pr, k)
+        L.populate(seed)
+        L.run_events(1)
+        fires += L.stats()["fires"]
+        made += L.counts()[1:]
+        assert L.check() == 0
+        L.close()
+    return fires, made
+
+
+def branching_pvalue(reactions, fires, made):
+    k = np.array([r[2] for r in reactions])
+    share = k / k.sum()
+    assert made.sum() == fires                  # every in-place conversion succeeds
+    return stats.chisquare(made, share * fires).pvalue
+
+
+def test_first_order_choice_branching_fractions():
+    # > 10^4 firings split over three in-place reactions in the ratio of
+    # their rate constants (Eq. 5), chi^2 over the three outcomes; and the
+    # share of each one alone within 4 binomial sigma
+    fires, made = branching_counts(THREE_WAY)
+    assert fires > 20000
+    assert branching_pvalue(THREE_WAY, fires, made) > 1e-3
+    k = np.array([r[2] for r in THREE_WAY])
+    for u, share in enumerate(k / k.sum()):
+        sd = math.sqrt(share * (1 - share) / fires)
+        assert abs(made[u] / fires - share) < 4 * sd, (u, made[u] / fires, share)
+
+
+@pytest.mark.parametrize("rule", [oracle.RULE_SYNC, oracle.RULE_SEQ_ID])
+@pytest.mark.parametrize("shape", ["one and two products", "two and two products"])
+def test_first_order_choice_exact(rule, shape):
+    # Two adjacent molecules of a species with two first-order reactions:
+    #   one and two products  A -> B (k1), A -> C + D (k2)
+    #   two and two products  A -> E + S, A -> E + P   (the enzyme-complex shape)
+    # at sum(k) tau = 0.5 with k2 = 2 k1; the exact one-event distribution
+    # weighs each reaction by k_u / sum(k) (Eq. 5).
+    if shape == "one and two products":
+        rx = [((0,), (1,), 2500.0), ((0,), (2, 3), 5000.0)]
+    else:
+        rx = [((0,), (1, 2), 2500.0), ((0,), (1, 3), 5000.0)]
+    m = Model((4, 4, 4), oracle.PERIODIC_ALL, [1e-12, 0.0, 0.0, 0.0], rx)
+    assert 0.3 < m.fire[0] < 0.5
+    a = vox(m, 1, 1, 1)
+    state = [(0, 0, a), (1, 0, m.nbr[a][4])]
+    exact = exact_sync(m, state, 0, 2) if rule == oracle.RULE_SYNC else exact_seq(m, state, 0, 2)
+    compare(exact, simulate(m, state, rule, TRIALS), TRIALS)
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS))
+def test_planted_choice_mistakes_fail_the_pins(plant, tmp_path):
+    from planted import planted_oracle, using
+    lib = planted_oracle(tmp_path, *PLANTS[plant])
+    with using(lib):
+        fires, made = branching_counts(THREE_WAY)
+        p_branch = branching_pvalue(THREE_WAY, fires, made)
+        rx = [((0,), (1,), 2500.0), ((0,), (2, 3), 5000.0)]
+        m = Model((4, 4, 4), oracle.PERIODIC_ALL, [1e-12, 0.0, 0.0, 0.0], rx)
+        a = vox(m, 1, 1, 1)
+        state = [(0, 0, a), (1, 0, m.nbr[a][4])]
+        exact = exact_sync(m, state, 0, 2)
+        obs = simulate(m, state, oracle.RULE_SYNC, TRIALS)
+    assert p_branch < 1e-6, "%s passed the branching pin (p=%.3g)" % (plant, p_branch)
+    if plant != "cut points not cumulative":   # with two reactions the first cut point is the same
+        with pytest.raises(AssertionError):
+            compare(exact, obs, TRIALS)

@@ -481,20 +481,32 @@ void psc_server_destroy(psc_server *S);
  *                    first_event the event index of the first event, so the
  *                    results equal psc_run_events on a lattice holding the
  *                    same molecules with the same seed (bit for bit).
- *   vox              device, n entries, in/out: voxel index of each molecule.
- *   ids              device, n entries, in: molecule ids.
+ *   vox              device, n entries, in/out: voxel index of each molecule;
+ *                    each in [0, ni*nj*nk) and no two equal.
+ *   ids              device, n entries, in: molecule ids, distinct and below
+ *                    0xFFFFFFFF (that value marks an unclaimed voxel).
  *   img              device, n entries, in/out: packed 16-bit wrap counters
  *                    (i bits 0-15, j 16-31, k 32-47); zeros if unused.
  *   n                molecules (the only occupied voxels of the lattice).
  *   stream           cudaStream_t (NULL = default stream).
- * Work is queued on the stream; the call returns once it is queued.  The first
- * call on each device looks up the addresses of the internal arrays
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  Every call clears the internal arrays it uses, but all calls on a
- * device share them: calls that may overlap on the GPU (different streams, or
- * host threads) race and must be serialised by the caller.
- * Errors: PSC_E_ARG, PSC_E_DIMS, PSC_E_FULL, PSC_E_LIMIT, PSC_E_CAPACITY,
- * PSC_E_CUDA.
+ * The call queues its work on the stream, waits for it (the stream is
+ * synchronised) and returns the status the device raised.  Every call first
+ * clears ni*nj*nk claim words and the vacancy mirror (about 4.5 bytes per
+ * voxel) and rebuilds the mirror from vox, so batch many events into one
+ * call.  The molecules are checked on the device while the mirror is built:
+ * an entry whose voxel is out of range or already taken, or whose id is
+ * 0xFFFFFFFF, is skipped, no event runs, the caller's buffers are left as
+ * they were and the call returns PSC_E_ARG.  Distinct ids are not checked:
+ * with two equal ids the results are undefined (every access stays in
+ * bounds).  The first call on each device looks up the addresses of the
+ * internal arrays (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture.  All calls on a device share the arrays, which
+ * keep the last call's contents: calls that may overlap on the GPU
+ * (different streams, or host threads) race and must be serialised by the
+ * caller.
+ * Errors: PSC_E_ARG (null buffer, bad species or flags, bad molecules as
+ * above), PSC_E_DIMS, PSC_E_FULL, PSC_E_LIMIT, PSC_E_CAPACITY (lattice above
+ * the limit), PSC_E_CUDA.
  */
 int psc_hop_events_static(int32_t ni, int32_t nj, int32_t nk, uint32_t boundary_flags,
                           uint64_t seed, int32_t species, uint32_t first_event, int32_t n_events,

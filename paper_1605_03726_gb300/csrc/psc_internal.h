@@ -24,6 +24,8 @@ constexpr int32_t kErrListOverflow = 1;
 constexpr int32_t kErrBirthOverflow = 2;
 constexpr int32_t kErrClaimTableFull = 4;
 constexpr int32_t kErrBarrierTimeout = 8;
+constexpr int32_t kErrBadInput = 16;       // caller-supplied molecules: voxel out of range,
+                                            // two on one voxel, or the reserved id
 
 // grid-wide barrier state of the persistent hop kernel: one arrival word whose
 // top bit flips each time every block has arrived
@@ -319,6 +321,11 @@ void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int3
 // set the vacancy-mirror bit of every molecule of a list (mirror cleared before)
 void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesList& list, const int32_t* count,
                              int blocks, cudaStream_t st);
+// the same for a list the library did not build: entries whose voxel is
+// outside [0, V), that land on a voxel already set, or whose id is kNoClaim
+// are skipped and raise kErrBadInput in *err
+void launch_mirror_from_list_checked(uint32_t* bits, const Geometry& geo, const SpeciesList& list,
+                                     const int32_t* count, int64_t V, int32_t* err, int blocks, cudaStream_t st);
 
 // ---- batched launches: many lattices (replicas) per launch ----
 // Item x covers blocks [block0, next block0) of the launch and runs the event

@@ -1398,6 +1398,29 @@ void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesL
     k_mirror_from_list<<<blocks, 256, 0, st>>>(bits, geo, list, count);
 }
 
+__global__ void k_mirror_from_list_checked(uint32_t* bits, Geometry G, const SpeciesList L, const int32_t* count,
+                                           int64_t V, int32_t* err)
+{
+    const int32_t n = *count;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const int32_t v = L.vox[x];
+        if (v < 0 || (int64_t)v >= V || L.ids[x] == kNoClaim) {
+            atomicOr(err, kErrBadInput);
+            continue;
+        }
+        int32_t i, j, k;
+        decode(G, (uint32_t)v, i, j, k);
+        const BitPos b = bitpos(G, i, j, k);
+        if (atomicOr(&bits[b.word], b.mask) & b.mask) atomicOr(err, kErrBadInput);   // a second molecule here
+    }
+}
+
+void launch_mirror_from_list_checked(uint32_t* bits, const Geometry& geo, const SpeciesList& list,
+                                     const int32_t* count, int64_t V, int32_t* err, int blocks, cudaStream_t st)
+{
+    k_mirror_from_list_checked<<<blocks, 256, 0, st>>>(bits, geo, list, count, V, err);
+}
+
 // ---------------------------------------------------------------------------
 // batched launches: every active replica runs its own next event (or list
 // pass) inside one launch; block b belongs to the item whose block range

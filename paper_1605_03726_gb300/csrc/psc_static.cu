@@ -79,6 +79,13 @@ __global__ void k_static_reset(int32_t n)
     }
 }
 
+// after the checked mirror build: a call whose molecules failed the checks
+// runs its events over zero molecules, so the caller's buffers stay as they were
+__global__ void k_static_gate()
+{
+    if (threadIdx.x == 0 && g_static_scalars.err != 0) g_static_scalars.counts[0] = 0;
+}
+
 }  // namespace
 }  // namespace psc
 
@@ -125,7 +132,9 @@ extern "C" int psc_hop_events_static(int32_t ni, int32_t nj, int32_t nk, uint32_
     list.ids = const_cast<uint32_t*>(ids);
     list.img = img;
     list.cap = n;
-    launch_mirror_from_list(sd->mirror, geo, list, &sd->scalars->counts[0], fill_blocks, st);
+    launch_mirror_from_list_checked(sd->mirror, geo, list, &sd->scalars->counts[0], V, &sd->scalars->err,
+                                    fill_blocks, st);
+    k_static_gate<<<1, 32, 0, st>>>();
 
     EventArgs a{};
     a.geo = geo;
@@ -149,5 +158,13 @@ extern "C" int psc_hop_events_static(int32_t ni, int32_t nj, int32_t nk, uint32_
         launch_claim(a, false, blocks, threads, st);
         launch_commit(a, false, blocks, threads, st);
     }
-    return cudaPeekAtLastError() == cudaSuccess ? PSC_OK : PSC_E_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return PSC_E_CUDA;
+    // wait for the events and report what the device raised (a plain copy of
+    // one word into host memory: no allocation)
+    int32_t err = 0;
+    if (cudaMemcpyAsync(&err, &sd->scalars->err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PSC_E_CUDA;
+    if (err & kErrBadInput) return PSC_E_ARG;
+    return err ? PSC_E_CAPACITY : PSC_OK;
 }

@@ -112,6 +112,7 @@ typedef struct {
     double run_ms;            /* persistent launches over stretches of events  */
     int64_t run_launches, run_events;
     int64_t tile_launches, tile_events;   /* of those, under the tile kernel   */
+    int64_t tile_lean_events;             /* of those, under its lean variant  */
 } psc_kernel_times;
 
 /* Tunables; zero in a field keeps the current value. */
@@ -181,6 +182,12 @@ typedef struct {
                                  only (else PSC_E_UNSUPPORTED at populate);
                                  periodic extents must be multiples of 4
                                  (PSC_E_DIMS).  -1 = synchronous (default)     */
+    int32_t tile_lean;        /* tile kernel variant: 1 = the lean kernel
+                                 wherever it applies (default: HCP lattices of
+                                 whole 4 x 4 x 2 bricks, boxes at least two
+                                 bricks thick, two or more boxes along every
+                                 periodic axis), -1 = always the general tile
+                                 kernel.  Same results either way              */
 } psc_options;
 
 /*

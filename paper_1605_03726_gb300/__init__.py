@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "resort_period", "block_threads", "blocks_per_sm", "collect_stats", "graph_events", "time_kernels",
         "claim_table", "persistent", "slot_map", "claim_slots", "run_per_thread", "barrier_timeout_us", "barrier_phantom", "tiles",
-        "tile_regions", "subvolume")]
+        "tile_regions", "subvolume", "tile_lean")]
 
 
 class KernelTimes(ctypes.Structure):
@@ -46,7 +46,8 @@ class KernelTimes(ctypes.Structure):
                 ("claim_launches", ctypes.c_int64), ("commit_launches", ctypes.c_int64),
                 ("reconcile_events", ctypes.c_int64), ("resorts", ctypes.c_int64),
                 ("run_ms", ctypes.c_double), ("run_launches", ctypes.c_int64), ("run_events", ctypes.c_int64),
-                ("tile_launches", ctypes.c_int64), ("tile_events", ctypes.c_int64)]
+                ("tile_launches", ctypes.c_int64), ("tile_events", ctypes.c_int64),
+                ("tile_lean_events", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))

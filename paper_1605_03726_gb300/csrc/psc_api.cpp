@@ -138,7 +138,7 @@ EventArgs event_args(const psc_lattice* L, int s)
     return a;
 }
 
-enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort, kSpanRun, kSpanTile };
+enum SpanKind { kSpanClaim = 0, kSpanCommit, kSpanReconcile, kSpanResort, kSpanRun, kSpanTile, kSpanTileLean };
 
 cudaEvent_t take_event(psc_lattice* L)
 {
@@ -368,6 +368,18 @@ bool tile_plan(psc_lattice* L, int s, TilePlan* P)
     const int64_t cap = std::min<int64_t>(best_work * 32, (int64_t)(2.0 * share * (double)L->sp[s].n0) + 8192);
     if (cap > INT32_MAX / 2) return false;
     best.cap = (int32_t)cap;
+    // the lean variant: HCP, whole bricks on every axis (so reflective walls
+    // fall on brick faces), boxes at least two bricks thick (neighbour waits),
+    // two or more boxes along every periodic axis (no box wraps onto itself)
+    {
+        const bool whole = (L->ni % 4) == 0 && (L->nj % 4) == 0 && (L->nk % 2) == 0;
+        const bool thick = nbi / best.pi >= 2 && nbj / best.pj >= 2 && nbk / best.pk >= 2;
+        const bool wraps = (!(L->bflags & PSC_PERIODIC_I) || best.pi >= 2) &&
+                           (!(L->bflags & PSC_PERIODIC_J) || best.pj >= 2) &&
+                           (!(L->bflags & PSC_PERIODIC_K) || best.pk >= 2);
+        best.lean = (!fcc && whole && thick && wraps && L->opt.tile_lean >= 0 &&
+                     lean_smem_bytes(best) <= L->tile_smem) ? 1 : 0;
+    }
     if (L->opt.tiles == 0) {
         if (L->tile_auto[s] == 0) L->tile_auto[s] = tile_balanced(L, s, best) ? 1 : -1;
         if (L->tile_auto[s] < 0) return false;
@@ -469,7 +481,7 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     launch_tile_scatter(A, sblocks, st);
     rc = cuda_fail(L, launch_tile_run(A, st));
     if (!rc) launch_tile_gather(A, st);
-    span_close(L, sp, kSpanTile, n_events);
+    span_close(L, sp, P.lean ? kSpanTileLean : kSpanTile, n_events);
     if (rc) return rc;
     L->launches += 3;
     L->events += (uint64_t)n_events;
@@ -1550,6 +1562,7 @@ int psc_set_options(psc_lattice* L, const psc_options* o)
         L->opt.subvolume = o->subvolume > 0 ? 1 : -1;
     }
     if (o->tile_regions) L->opt.tile_regions = o->tile_regions < 0 ? 0 : o->tile_regions;
+    if (o->tile_lean) L->opt.tile_lean = o->tile_lean > 0 ? 1 : -1;
     if (o->slot_map) {
         if (o->slot_map < 1 || o->slot_map > 3) return PSC_E_ARG;
         L->opt.slot_map = o->slot_map;
@@ -1578,8 +1591,10 @@ int psc_kernel_times_get(psc_lattice* L, psc_kernel_times* out)
         case kSpanReconcile: out->reconcile_ms += ms; out->reconcile_events++; break;
         case kSpanRun: out->run_ms += ms; out->run_launches++; out->run_events += sp.events; break;
         case kSpanTile:
+        case kSpanTileLean:
             out->run_ms += ms; out->run_launches++; out->run_events += sp.events;
             out->tile_launches++; out->tile_events += sp.events;
+            if (sp.kind == kSpanTileLean) out->tile_lean_events += sp.events;
             break;
         default: out->resort_ms += ms; out->resorts++; break;
         }

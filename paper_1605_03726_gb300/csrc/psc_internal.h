@@ -185,6 +185,8 @@ struct TilePlan {
     int32_t box_words;         // (ei + 2)(ej + 2)(ek + 2): region plus one brick of halo
     int32_t cap;               // molecule slots per region (bucket, inbox)
     int32_t fcc;               // FCC lattice: stencil and neighbourhood masks by k mod 3
+    int32_t lean;              // 1: the stretch runs k_tile_lean (HCP, whole bricks, boxes of
+                               // at least two bricks, two or more boxes along periodic axes)
 };
 
 // A stretch of a species without reactions under the tile kernel.  Each
@@ -269,6 +271,15 @@ inline int tile_smem_bytes(const TilePlan& P)
 {
     return ((P.box_words + 3) & ~3) * 4 + (P.fcc ? 96 : 32) * 8 * 4 + kTileOutbox * 12 + kTileQueue * 4 +
            ((P.nbi + P.nbj + P.nbk + 15) & ~15);
+}
+// the lean tile kernel: shared-memory tables per (place in the brick word,
+// direction), per-axis halo tables, plus the areas of the general kernel
+constexpr int kLeanEntries = 32 * 12;
+inline int lean_smem_bytes(const TilePlan& P)
+{
+    const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
+    return ((P.box_words + 3) & ~3) * 4 + kLeanEntries * 8 * 4 + kLeanEntries * 2 * 4 + kTileOutbox * 12 +
+           kTileQueue * 4 + halo_tables * 4 + ((P.nbi + P.nbj + P.nbk + 15) & ~15);
 }
 constexpr int kTileThreads = 512;
 constexpr int kTileBlocksPerSM = 2;

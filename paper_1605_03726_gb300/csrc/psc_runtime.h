@@ -91,7 +91,7 @@ struct psc_lattice {
     std::vector<int> reconcile[kMaxSpecies];
     uint64_t since_resort[kMaxSpecies] = {};
 
-    psc_options opt{64, 256, 8, 0, 32, 0, 0, 1, 1, 3, 0, 1000000, 0, 0, 0, -1};
+    psc_options opt{64, 256, 8, 0, 32, 0, 0, 1, 1, 3, 0, 1000000, 0, 0, 0, -1, 1};
     int64_t launches = 0;
     uint64_t events = 0;
     uint64_t h2d = 0, d2h = 0;

@@ -922,8 +922,11 @@ static cudaError_t launch_tile_run_t(const TileArgs& A, cudaStream_t st)
                                        smem, st);
 }
 
+#include "psc_tiles_lean.cuh"
+
 cudaError_t launch_tile_run(const TileArgs& A, cudaStream_t st)
 {
+    if (A.plan.lean) return launch_tile_lean(A, st);
     return A.plan.fcc ? launch_tile_run_t<true>(A, st) : launch_tile_run_t<false>(A, st);
 }
 

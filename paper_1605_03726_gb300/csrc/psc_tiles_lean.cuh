@@ -1,0 +1,512 @@
+// psc_tiles_lean.cuh -- the tile kernel for its common case: HCP lattices of
+// whole mirror bricks (ni, nj multiples of 4, nk even) cut into boxes at
+// least two bricks thick, never a single box along a periodic axis.  Part of
+// psc_kernels.cu's translation unit (after psc_tiles.cuh, whose plan, bucket,
+// inbox, neighbour-wait and hand-over helpers it shares).
+//
+// Same owner-computes protocol and the same results as k_tile_run (Sec. 2.3,
+// synchronous rule), with less work per molecule:
+//   - every (place c of the molecule in its brick word, direction d) is looked
+//     up in tables built once per launch in shared memory: the packed step of
+//     the box coordinates, and the eight-word window around the target with
+//     the masks of the target and of its twelve neighbours (Sec. 2.1) minus
+//     the mover itself, so "the target is vacant and nobody else can reach
+//     it" is one OR over eight masked box words;
+//   - words behind a reflective wall hold all ones in the box, so no hop
+//     needs a bounds test (a wall voxel looks occupied: the hop fails, and a
+//     target next to a wall takes the claim path, which gives the same result);
+//   - the halo refresh indexes the global mirror through per-axis tables of
+//     global brick coordinates instead of per-word wrap arithmetic;
+//   - hops inside the box update the box (and, for the outermost brick layer,
+//     the global mirror) inline; claim read-backs and departures go to the
+//     deferred queue as before.
+
+constexpr uint32_t kLeanOff = 4u | (4u << 11) | (2u << 22);   // region -> box coordinates
+
+struct LeanShared {
+    uint32_t* box;
+    uint4* tmask;              // [kLeanEntries][2]: masks of the eight-word window
+    int32_t* tstep;            // [kLeanEntries]: packed step dx + 2048 dy + 4194304 dz
+    int32_t* tbase;            // [kLeanEntries]: first window word minus the mover's word
+    int32_t* o_t;              // outbox: departures of an event
+    uint32_t* o_id;
+    int32_t* o_q;
+    int32_t* queue;            // bucket slots whose handling is deferred
+    int32_t* hx;               // global brick coordinate of box word coordinate x (-1: wall)
+    int32_t* hy;
+    int32_t* hz;
+    uint8_t* own;              // owner tables
+};
+
+__device__ __forceinline__ LeanShared lean_shared(uint32_t* smem, const TilePlan& P, const TileBox& b)
+{
+    LeanShared S;
+    S.box = smem;
+    S.tmask = reinterpret_cast<uint4*>(smem + ((P.box_words + 3) & ~3));
+    S.tstep = reinterpret_cast<int32_t*>(S.tmask + 2 * kLeanEntries);
+    S.tbase = S.tstep + kLeanEntries;
+    S.o_t = S.tbase + kLeanEntries;
+    S.o_id = reinterpret_cast<uint32_t*>(S.o_t + kTileOutbox);
+    S.o_q = S.o_t + 2 * kTileOutbox;
+    S.queue = S.o_t + 3 * kTileOutbox;
+    S.hx = S.queue + kTileQueue;
+    S.hy = S.hx + b.BI;
+    S.hz = S.hy + b.BJ;
+    const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
+    S.own = reinterpret_cast<uint8_t*>(S.hx + halo_tables);
+    return S;
+}
+
+// box word index and place of packed box coordinates bx | by << 11 | bz << 22
+__device__ __forceinline__ int lean_word(uint32_t p, int BI, int BIJ)
+{
+    return (int)(p >> 23) * BIJ + (int)((p >> 13) & 0x1FFu) * BI + (int)((p >> 2) & 0x1FFu);
+}
+__device__ __forceinline__ uint32_t lean_place(uint32_t p)
+{
+    return (p & 3u) | ((p >> 9) & 0xCu) | ((p >> 18) & 0x10u);
+}
+
+// Is the box word of packed coordinates p in the region's outermost brick
+// layer (read by neighbouring boxes as halo)?  p must lie in the region.
+__device__ __forceinline__ bool lean_outer(uint32_t p, const TileBox& b)
+{
+    const uint32_t wx = (p >> 2) & 0x1FFu, wy = (p >> 13) & 0x1FFu, wz = p >> 23;
+    return (wx - 2u) >= (uint32_t)(b.ei - 2) || (wy - 2u) >= (uint32_t)(b.ej - 2) ||
+           (wz - 2u) >= (uint32_t)(b.ek - 2);
+}
+
+// global mirror word of the region word holding packed coordinates p
+__device__ __forceinline__ int64_t lean_gword(uint32_t p, const TilePlan& P, int64_t gbase)
+{
+    const int wx = (int)((p >> 2) & 0x1FFu), wy = (int)((p >> 13) & 0x1FFu), wz = (int)(p >> 23);
+    return gbase + ((int64_t)wz * P.nbj + wy) * P.nbi + wx;
+}
+
+__device__ void lean_build_tables(const TileBox& b, const TilePlan& P, const Geometry& G, const LeanShared& S)
+{
+    const int BI = b.BI, BIJ = b.BI * b.BJ;
+    for (int e = threadIdx.x; e < kLeanEntries; e += blockDim.x) {
+        const int c = e / 12, d = e - 12 * c;
+        const int x = 4 + (c & 3), y = 4 + ((c >> 2) & 3), z = 2 + ((c >> 4) & 1);
+        int dx, dy, dz;
+        tile_step(d, y, z, -1, dx, dy, dz);
+        const int tx = x + dx, ty = y + dy, tz = z + dz;
+        S.tstep[e] = dx + dy * 2048 + dz * 4194304;
+        const int wx0 = (tx - 1) >> 2, wy0 = (ty - 1) >> 2, wz0 = (tz - 1) >> 1;
+        S.tbase[e] = (wz0 - (z >> 1)) * BIJ + (wy0 - (y >> 2)) * BI + (wx0 - (x >> 2));
+        uint32_t m[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int d2 = -1; d2 < 12; ++d2) {
+            int ex = 0, ey = 0, ez = 0;
+            if (d2 >= 0) tile_step(d2, ty, tz, -1, ex, ey, ez);
+            const int nx = tx + ex, ny = ty + ey, nz = tz + ez;
+            if (nx == x && ny == y && nz == z) continue;          // the mover itself
+            const int q = ((nx >> 2) - wx0) | (((ny >> 2) - wy0) << 1) | (((nz >> 1) - wz0) << 2);
+            m[q] |= 1u << ((nx & 3) | ((ny & 3) << 2) | ((nz & 1) << 4));
+        }
+        S.tmask[2 * e] = make_uint4(m[0], m[1], m[2], m[3]);
+        S.tmask[2 * e + 1] = make_uint4(m[4], m[5], m[6], m[7]);
+    }
+    // per-axis global brick coordinates of the box word coordinates, wrapped
+    // along periodic axes, -1 behind a reflective wall
+    for (int q = threadIdx.x; q < b.BI + b.BJ + b.BK; q += blockDim.x) {
+        int a, w, first, nb;
+        if (q < b.BI) { a = 0; w = q; first = b.bi0; nb = P.nbi; }
+        else if (q < b.BI + b.BJ) { a = 1; w = q - b.BI; first = b.bj0; nb = P.nbj; }
+        else { a = 2; w = q - b.BI - b.BJ; first = b.bk0; nb = P.nbk; }
+        int g = first - 1 + w;
+        if (g < 0 || g >= nb) g = (G.bflags & (1u << a)) ? (g < 0 ? g + nb : g - nb) : -1;
+        S.hx[q] = g;                       // hx, hy, hz are consecutive
+    }
+}
+
+// Refresh the halo (box words outside the region) from the global mirror;
+// words behind a reflective wall are all ones.  Halo word q: first the two
+// z faces (full planes), then the full rows of the two y faces, then the end
+// words of the other rows; each thread issues its loads in groups of eight.
+__device__ __forceinline__ void lean_refresh_halo(const TilePlan& P, const TileBox& b, const LeanShared& S,
+                                                  const FastDiv& div_bi, const FastDiv& div_bj2,
+                                                  const uint32_t* bits, bool initial)
+{
+    const int BI = b.BI, BJ = b.BJ, BK = b.BK, BIJ = BI * BJ;
+    const int n_z = 2 * BIJ;
+    const int n_y = n_z + 2 * (BK - 2) * BI;
+    const int total = n_y + 2 * (BK - 2) * (BJ - 2);
+    constexpr int H = 8;
+    for (int q0 = threadIdx.x; q0 < total; q0 += H * blockDim.x) {
+        int idx[H];
+        uint32_t val[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int q = q0 + h * blockDim.x;
+            idx[h] = -1;
+            val[h] = ~0u;
+            if (q >= total) continue;
+            int wx, wy, wz;
+            if (q < n_z) {
+                const int f = q >= BIJ ? 1 : 0;
+                const int r = q - f * BIJ;
+                wy = (int)fdiv((uint32_t)r, div_bi);
+                wx = r - wy * BI;
+                wz = f ? BK - 1 : 0;
+            } else if (q < n_y) {
+                const int r2 = q - n_z;
+                const int row = (int)fdiv((uint32_t)r2, div_bi);
+                wx = r2 - row * BI;
+                wz = 1 + (row >> 1);
+                wy = (row & 1) ? BJ - 1 : 0;
+            } else {
+                const int r3 = q - n_y;
+                const int col = (int)fdiv((uint32_t)r3, div_bj2);
+                wy = 1 + r3 - col * (BJ - 2);
+                wz = 1 + (col >> 1);
+                wx = (col & 1) ? BI - 1 : 0;
+            }
+            const int gi = S.hx[wx], gj = S.hy[wy], gk = S.hz[wz];
+            idx[h] = (wz * BJ + wy) * BI + wx;
+            if ((gi | gj | gk) >= 0) {
+                val[h] = __ldcg(&bits[((int64_t)gk * P.nbj + gj) * P.nbi + gi]);
+            } else if (!initial) {
+                idx[h] = -1;              // walls never change
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            if (idx[h] >= 0) S.box[idx[h]] = val[h];
+    }
+}
+
+// A molecule of the box (packed box coordinates p, place c) moves to packed
+// box coordinates t inside its region: box bits, and the global mirror for
+// words of the outermost layer.
+__device__ __forceinline__ void lean_move_inside(const TileArgs& A, const TileBox& b, uint32_t* box, int BI, int BIJ,
+                                                 int64_t gbase, uint32_t p, uint32_t c, uint32_t t)
+{
+    const int wv = lean_word(p, BI, BIJ), wt = lean_word(t, BI, BIJ);
+    const uint32_t mv = 1u << c, mt = 1u << lean_place(t);
+    const bool vo = lean_outer(p, b), to = lean_outer(t, b);
+    if (wv == wt) {
+        atomicXor(&box[wv], mv | mt);
+        if (vo) atomicXor(&A.ev.bits[lean_gword(p, A.plan, gbase)], mv | mt);
+    } else {
+        atomicXor(&box[wv], mv);
+        atomicXor(&box[wt], mt);
+        if (vo) atomicXor(&A.ev.bits[lean_gword(p, A.plan, gbase)], mv);
+        if (to) atomicXor(&A.ev.bits[lean_gword(t, A.plan, gbase)], mt);
+    }
+}
+
+// A molecule (packed box coordinates p, place c) leaves its region for
+// packed box coordinates t: its bit leaves the box and the global mirror, the
+// target's bit is set in the global mirror (the owner's box picks it up with
+// the arrival), wrap counters follow a periodic wrap, and the molecule goes
+// to the outbox (or straight to the inbox when the outbox is full).
+__device__ __forceinline__ void lean_depart(const TileArgs& A, const TileBox& b, const LeanShared& S, int BI,
+                                            int BIJ, int64_t gbase, int* s_out_n, uint32_t p, uint32_t c, uint32_t t,
+                                            uint32_t id)
+{
+    const Geometry& G = A.ev.geo;
+    int32_t gi, gj, gk;
+    uint64_t wr;
+    tile_global(G, b, (int)(t & 0x7FFu), (int)((t >> 11) & 0x7FFu), (int)(t >> 22), gi, gj, gk, wr);
+    if (wr) {
+        uint64_t* wp = &A.img_id[id - A.id_lo];
+        *wp = img_add(*wp, wr);
+    }
+    const uint32_t mv = 1u << c;
+    atomicXor(&S.box[lean_word(p, BI, BIJ)], mv);
+    atomicXor(&A.ev.bits[lean_gword(p, A.plan, gbase)], mv);   // the source is in the outermost layer
+    const BitPos gt = bitpos(G, gi, gj, gk);
+    atomicXor(&A.ev.bits[gt.word], gt.mask);
+    const int q = tile_region_of(A.plan, S.own, gi, gj, gk);
+    const int32_t tv = gi + G.ni * (gj + G.nj * gk);
+    const int o = atomicAdd(s_out_n, 1);
+    if (o < kTileOutbox) {
+        S.o_t[o] = tv;
+        S.o_id[o] = id;
+        S.o_q[o] = q;
+    } else {
+        const int cap = A.plan.cap;
+        const int slot = atomicAdd(&A.in_cnt[q], 1);
+        if (slot < cap) {
+            A.in_vox[(int64_t)q * cap + slot] = tv;
+            A.in_ids[(int64_t)q * cap + slot] = id;
+        } else {
+            atomicOr(&A.ev.sc->err, kErrListOverflow);
+        }
+    }
+}
+
+// global voxel index of packed box coordinates t (a target next to the region)
+__device__ __forceinline__ int32_t lean_voxel(const Geometry& G, const TileBox& b, uint32_t t)
+{
+    int32_t i, j, k;
+    uint64_t wr;
+    tile_global(G, b, (int)(t & 0x7FFu), (int)((t >> 11) & 0x7FFu), (int)(t >> 22), i, j, k, wr);
+    return i + G.ni * (j + G.nj * k);
+}
+
+// Claim-phase decision: bits 0-3 the direction, kTileMove (no claim needed)
+// or kTileClaimed (claimed in the global words); neither: the hop fails.
+__global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(const TileArgs A)
+{
+    extern __shared__ uint32_t smem[];
+    // s_misc: arrivals, survivors, outbox entries, wait flag, -, commit queue
+    __shared__ int s_misc[6];
+    const EventArgs& a = A.ev;
+    const Geometry& G = a.geo;
+    const TilePlan& P = A.plan;
+    const int r = blockIdx.x;
+    const TileBox b = tile_box(P, r);
+    const LeanShared S = lean_shared(smem, P, b);
+    uint32_t* box = S.box;
+    const int BI = b.BI, BIJ = b.BI * b.BJ;
+    const int cap = P.cap;
+    const int64_t base = (int64_t)r * cap;
+    const uint32_t c2 = ((uint32_t)a.s << 4) | kTagEvent;
+    uint32_t* claim = A.claim;
+    const int64_t gbase = ((int64_t)(b.bk0 - 1) * P.nbj + (b.bj0 - 1)) * P.nbi + (b.bi0 - 1);
+    const uint32_t rxn = 4u * (uint32_t)b.ei, ryn = 4u * (uint32_t)b.ej, rzn = 2u * (uint32_t)b.ek;
+    const FastDiv div_bi = tile_fastdiv((uint32_t)b.BI), div_bj2 = tile_fastdiv((uint32_t)(b.BJ - 2));
+    constexpr int U = 2;                                 // molecules whose memory operations go out together
+    tile_build_owners(P, S.own);
+    lean_build_tables(b, P, G, S);
+    __syncthreads();
+    // region words from the global mirror, then the halo
+    for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
+        const int wx = 1 + q % b.ei, wy = 1 + (q / b.ei) % b.ej, wz = 1 + q / (b.ei * b.ej);
+        box[(wz * b.BJ + wy) * BI + wx] = __ldcg(&a.bits[tile_region_word(P, b, wx, wy, wz)]);
+    }
+    lean_refresh_halo(P, b, S, div_bi, div_bj2, a.bits, true);
+    int n = *((volatile int32_t*)&A.b_cnt[r]);
+    // the scatter left voxel indices: store coordinates relative to the region
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        int32_t i, j, k;
+        decode(G, (uint32_t)A.b_vox[0][base + x], i, j, k);
+        A.b_vox[0][base + x] = (int32_t)tile_pack(i - 4 * b.bi0, j - 4 * b.bj0, k - 2 * b.bk0);
+    }
+    unsigned long long n_att = 0, n_hop = 0;
+    __syncthreads();
+    for (int e = 0; e < A.n_events; ++e) {
+        const uint32_t g = a.g + (uint32_t)e;
+        const int cur = e & 1;
+        const int32_t* bv = A.b_vox[cur] + base;
+        const uint32_t* bi = A.b_ids[cur] + base;
+        uint32_t* bs = A.b_state + base;
+        if (e > 0) {
+            // the neighbours' last commits: halo bits, arrivals, reset claim words
+            if (!tile_wait_neighbours(A, A.done, r, (uint32_t)e, &s_misc[3])) return;
+            tile_ingest(A, r, b, box, n, cur, s_misc);
+            lean_refresh_halo(P, b, S, div_bi, div_bj2, a.bits, false);
+            __syncthreads();
+        }
+        // ---- claim phase ----
+        for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
+            uint32_t vv[U], ii[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int x = c0 + u * blockDim.x + threadIdx.x;
+                vv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+                ii[u] = x < n ? __ldcg(bi + x) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int xm = c0 + u * blockDim.x + threadIdx.x;
+                if (xm >= n) continue;
+                const uint32_t p = vv[u] + kLeanOff;
+                uint32_t rnd[4];
+                philox(ii[u], g, c2, 0u, a.key0, a.key1, rnd);
+                const uint32_t d = __umulhi(rnd[0], 12u);
+                const int e12 = (int)(lean_place(p) * 12u + d);
+                const int w0 = lean_word(p, BI, BIJ) + S.tbase[e12];
+                const uint4 m0 = S.tmask[2 * e12], m1 = S.tmask[2 * e12 + 1];
+                const uint32_t busy = (box[w0] & m0.x) | (box[w0 + 1] & m0.y) | (box[w0 + BI] & m0.z) |
+                                      (box[w0 + BI + 1] & m0.w) | (box[w0 + BIJ] & m1.x) |
+                                      (box[w0 + BIJ + 1] & m1.y) | (box[w0 + BIJ + BI] & m1.z) |
+                                      (box[w0 + BIJ + BI + 1] & m1.w);
+                uint32_t st = d;
+                if (busy == 0u) {
+                    st |= kTileMove;                     // vacant, and only the mover is next to it
+                } else {
+                    const uint32_t t = p + (uint32_t)S.tstep[e12];
+                    if (!(box[lean_word(t, BI, BIJ)] & (1u << lean_place(t)))) {
+                        // vacant, but other molecules can reach it: the lowest id wins
+                        atomicMin(&claim[lean_voxel(G, b, t)], ii[u]);
+                        st |= kTileClaimed;
+                    }
+                }
+                bs[xm] = st;
+            }
+        }
+        n_att += (unsigned long long)n;
+        if (threadIdx.x == 0) {
+            s_misc[1] = 0;
+            s_misc[2] = 0;
+            s_misc[5] = 0;
+        }
+        // a claim word is touched only by boxes that are all neighbours of each other
+        tile_publish(A.claimed, r, (uint32_t)(e + 1));
+        if (!tile_wait_neighbours(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;
+        // ---- commit phase: hops inside the region here, everything else queued ----
+        int32_t* ov = A.b_vox[cur ^ 1] + base;
+        uint32_t* oi = A.b_ids[cur ^ 1] + base;
+        for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
+            uint32_t vv[U], ii[U], ss[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int x = c0 + u * blockDim.x + threadIdx.x;
+                vv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+                ii[u] = x < n ? __ldcg(bi + x) : 0u;
+                ss[u] = x < n ? __ldcg(bs + x) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int xm = c0 + u * blockDim.x + threadIdx.x;
+                const uint32_t st = ss[u];
+                uint32_t w = vv[u];
+                bool keep = xm < n;
+                bool defer = (st & kTileClaimed) != 0u;
+                if (st & kTileMove) {
+                    const uint32_t p = w + kLeanOff;
+                    const uint32_t c = lean_place(p);
+                    const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
+                    if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn && ((t >> 22) - 2u) < rzn) {
+                        lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
+                        w = t - kLeanOff;
+                        ++n_hop;
+                    } else {
+                        defer = true;
+                    }
+                }
+                if (defer) {
+                    const int k = atomicAdd(&s_misc[5], 1);
+                    if (k < kTileQueue) {
+                        S.queue[k] = xm;
+                        keep = false;
+                    } else {
+                        // queue full: handle it here
+                        const uint32_t p = w + kLeanOff;
+                        const uint32_t c = lean_place(p);
+                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
+                        bool win = (st & kTileMove) != 0u;
+                        if (!win) {
+                            const int32_t tv = lean_voxel(G, b, t);
+                            win = __ldcg(&claim[tv]) == ii[u];
+                            if (win) claim[tv] = kNoClaim;
+                        }
+                        if (win) {
+                            ++n_hop;
+                            if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn &&
+                                ((t >> 22) - 2u) < rzn) {
+                                lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
+                                w = t - kLeanOff;
+                            } else {
+                                lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
+                                keep = false;
+                            }
+                        }
+                    }
+                }
+                tile_keep(keep, w, ii[u], &s_misc[1], ov, oi);
+            }
+        }
+        __syncthreads();
+        {
+            // queued molecules: claim read-backs of a batch in flight together
+            const int m = min(s_misc[5], kTileQueue);
+            for (int c0 = 0; c0 < m; c0 += U * blockDim.x) {
+                int32_t xx[U], tv[U];
+                uint32_t vv[U], ii[U], ss[U], rb[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = c0 + u * blockDim.x + threadIdx.x;
+                    xx[u] = k < m ? S.queue[k] : -1;
+                    vv[u] = xx[u] >= 0 ? (uint32_t)__ldcg(bv + xx[u]) : 0u;
+                    ii[u] = xx[u] >= 0 ? __ldcg(bi + xx[u]) : 0u;
+                    ss[u] = xx[u] >= 0 ? __ldcg(bs + xx[u]) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    rb[u] = 0u;
+                    tv[u] = -1;
+                    if (!(ss[u] & kTileClaimed)) continue;
+                    const uint32_t p = vv[u] + kLeanOff;
+                    const uint32_t t = p + (uint32_t)S.tstep[lean_place(p) * 12u + (ss[u] & 15u)];
+                    tv[u] = lean_voxel(G, b, t);
+                    rb[u] = __ldcg(&claim[tv[u]]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t st = ss[u];
+                    uint32_t w = vv[u];
+                    bool keep = xx[u] >= 0;
+                    bool win = (st & kTileMove) != 0u;
+                    if ((st & kTileClaimed) && rb[u] == ii[u]) {
+                        win = true;
+                        claim[tv[u]] = kNoClaim;         // the winner resets the word
+                    }
+                    if (keep && win) {
+                        const uint32_t p = w + kLeanOff;
+                        const uint32_t c = lean_place(p);
+                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
+                        ++n_hop;
+                        if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn &&
+                            ((t >> 22) - 2u) < rzn) {
+                            lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
+                            w = t - kLeanOff;
+                        } else {
+                            lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
+                            keep = false;
+                        }
+                    }
+                    tile_keep(keep, w, ii[u], &s_misc[1], ov, oi);
+                }
+            }
+        }
+        __syncthreads();
+        n = s_misc[1];
+        // the outbox to the inboxes of the boxes the molecules entered
+        {
+            const int m = min(s_misc[2], kTileOutbox);
+            for (int o = threadIdx.x; o < m; o += blockDim.x) {
+                const int q = S.o_q[o];
+                const int slot = atomicAdd(&A.in_cnt[q], 1);
+                if (slot < cap) {
+                    A.in_vox[(int64_t)q * cap + slot] = S.o_t[o];
+                    A.in_ids[(int64_t)q * cap + slot] = S.o_id[o];
+                } else {
+                    atomicOr(&a.sc->err, kErrListOverflow);
+                }
+            }
+        }
+        tile_publish(A.done, r, (uint32_t)(e + 1));
+    }
+    // the last event's arrivals, then the region's bits back to the mirror
+    if (A.n_events > 0 && !tile_wait_neighbours(A, A.done, r, (uint32_t)A.n_events, &s_misc[3])) return;
+    if (A.n_events > 0) tile_ingest(A, r, b, box, n, A.n_events & 1, s_misc);
+    __syncthreads();
+    for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
+        const int wx = 1 + q % b.ei, wy = 1 + (q / b.ei) % b.ej, wz = 1 + q / (b.ei * b.ej);
+        a.bits[tile_region_word(P, b, wx, wy, wz)] = box[(wz * b.BJ + wy) * BI + wx];
+    }
+    if (threadIdx.x == 0) A.b_cnt[r] = n;
+    if (a.collect_stats) {
+        if (threadIdx.x == 0) atomicAdd(&a.sc->stats[kStatAttempts], n_att);
+        flush_stat(&a.sc->stats[kStatHops], n_hop);
+    }
+}
+
+static cudaError_t launch_tile_lean(const TileArgs& A, cudaStream_t st)
+{
+    const size_t smem = (size_t)lean_smem_bytes(A.plan);
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_tile_lean, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    void* args[] = {const_cast<TileArgs*>(&A)};
+    return cudaLaunchCooperativeKernel((const void*)k_tile_lean, dim3(A.plan.regions), dim3(kTileThreads), args, smem,
+                                       st);
+}

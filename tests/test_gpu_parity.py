@@ -226,6 +226,40 @@ def test_diffusion_512cubed_full_size():
         assert_same(g, o, chunk)
 
 
+@pytest.mark.slow
+def test_crowded_reversible_256cubed_full_size():
+    # the crowded reversible workload at its full size: 256^3 with reflective
+    # walls, 30 % immobile crowders, A 5 % (5 um^2/s), B 1 % (1 um^2/s),
+    # A + B <-> C (kf = 1e-19 m^3/s, kb = 10 /s, C 0.5 um^2/s).  200 events:
+    # A's list is re-sorted after 64 of its events, every A and B event reacts
+    # (reconcile passes over lists sized for the lattice), C molecules fire
+    # back (births); hash claim tables at this size
+    V = 256 ** 3
+    g, o = build_both((256, 256, 256), lambda L: models.crowded_reversible(L, V), 1, boundary=0)
+    for chunk in (5, 70, 125):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+    st = o.stats()
+    assert st["reactions2"] > 0 and st["reactions1"] > 0
+
+
+@pytest.mark.slow
+def test_mapk_like_200cubed_full_size():
+    # the MAPK-like cascade at its full size: 200^3 periodic, three tiers of
+    # dual phosphorylation with phosphatases (22 species, 30 reactions, counts,
+    # D and rates drawn from the seed); 10^4 events (about 14 ms of simulated
+    # time) cross many re-sorts of the fastest species, and complexes form,
+    # dissociate and convert (reconcile passes, births)
+    g, o = build_both((200, 200, 200), lambda L: models.mapk_like(L, 5), 1)
+    for chunk in (10, 1990, 8000):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+    st = o.stats()
+    assert st["reactions2"] > 0 and st["reactions1"] > 0
+
+
 # Owner-computes tile kernel (forced on, with a given number of boxes): every
 # stretch scatters the list into boxes, runs, and gathers it back; molecules
 # cross boxes every event.  Shapes: periodic with whole bricks, reflective
@@ -251,6 +285,37 @@ def test_tile_kernel_matches_oracle(shape, boundary, frac, regions, claim_table)
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, chunk)
+
+
+# The lean tile kernel (HCP lattices of whole bricks, boxes of two or more
+# bricks, several boxes along periodic axes): the same cases with both tile
+# kernels forced, each bit-exact against the oracle, and the lean kernel
+# shown to have run where it applies.
+LEAN_CASES = [
+    ((64, 64, 64), psc.PERIODIC_ALL, 0.30, 12),
+    ((96, 64, 40), psc.PERIODIC_ALL, 0.01, 16),
+    ((96, 64, 40), psc.PERIODIC_ALL, 0.05, 0),
+    ((48, 40, 36), 0, 0.10, 0),
+    ((48, 40, 36), 0, 0.60, 5),
+    ((40, 32, 22), psc.PERIODIC_I, 0.20, 12),
+    ((32, 24, 18), psc.PERIODIC_J | psc.PERIODIC_K, 0.15, 18),
+    ((56, 48, 30), psc.PERIODIC_I | psc.PERIODIC_K, 0.02, 27),
+]
+
+
+@pytest.mark.parametrize("lean", [1, -1])
+@pytest.mark.parametrize("shape,boundary,frac,regions", LEAN_CASES)
+def test_lean_tile_kernel_matches_oracle(shape, boundary, frac, regions, lean):
+    n = max(1, int(frac * shape[0] * shape[1] * shape[2]))
+    g, o = build_both(shape, lambda L: models.diffusion_only(L, n), 31, boundary=boundary,
+                      claim_table=1, tiles=1, tile_regions=regions, tile_lean=lean, time_kernels=1)
+    for chunk in (1, 6, 45):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, chunk)
+    kt = g.kernel_times()
+    assert kt["tile_events"] == 52
+    assert (kt["tile_lean_events"] == 52) if lean > 0 else (kt["tile_lean_events"] == 0)
 
 
 def _walkers_and_crowders(L, V):

@@ -55,7 +55,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--replicas", type=int, default=512, help="replicas of the serving workload")
-    ap.add_argument("--serial-sample", type=int, default=16, help="replicas timed one at a time")
+    ap.add_argument("--serial-sample", type=int, default=0,
+                    help="replicas timed one at a time (0: all of them, the same set as the batched run)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the reaction workloads (A + B -> C 64^3, crowded 256^3, MAPK-like 200^3)")
+    ap.add_argument("--config-events", type=int, default=0,
+                    help="events of the crowded and MAPK-like workloads (0: 650 and 4000)")
     ap.add_argument("--compartments", default="none", choices=["none", "cell"],
                     help="cell: the same lattice holding a round cell (outside, membrane, cytoplasm) "
                          "with the walkers in its cytoplasm")
@@ -64,6 +69,8 @@ def parse():
                          "periodic ABC stacking in whole bricks)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "list"],
                     help="stretch kernel: the library's choice, the tile kernel, or the molecule-list kernel")
+    ap.add_argument("--tile-kernel", default="auto", choices=["auto", "general"],
+                    help="tile kernel variant: the lean kernel where it applies, or always the general one")
     ap.add_argument("--rule", default="sync", choices=["sync", "subvolume"],
                     help="update rule: synchronous claims (the paper's hot path on the GPU), or the "
                          "sub-volume colouring rule (Sec. 2.5), for comparison")
@@ -254,6 +261,8 @@ def model(psc, L, args):
     L.set_options(resort_period=RESORT_PERIOD)
     if args.kernel != "auto":
         L.set_options(tiles=1 if args.kernel == "tile" else -1)
+    if args.tile_kernel == "general":
+        L.set_options(tile_lean=-1)
     if args.rule == "subvolume":
         L.set_options(subvolume=1)
 
@@ -354,6 +363,9 @@ def gpu_arm(args, rank, world, local):
         "bytes_alg_per_launch": round(b_alg * N_MOL * events_per_launch),
         "kernel": ("k_subvol_run (sub-volume rule: eight colour passes per event, rounds per colour)"
                    if args.rule == "subvolume" else
+                   "k_tile_lean (owner-computes boxes in shared memory, table-driven neighbourhood test, "
+                   "neighbour waits; one launch per stretch, with k_tile_scatter / k_tile_gather)"
+                   if kt.get("tile_lean_events", 0) > 0 else
                    "k_tile_run (owner-computes boxes in shared memory, neighbour waits; one launch per stretch, "
                    "with k_tile_scatter / k_tile_gather)" if tiles_used
                    else "k_hop_run (persistent: claim phase, grid barrier, commit phase per event)" if persistent
@@ -382,7 +394,7 @@ def kernel_revision():
     """Hash of the kernel sources: ncu traffic is reported only for the kernels it was taken on."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("psc_kernels.cu", "psc_tiles.cuh", "psc_internal.h"):
+    for name in ("psc_kernels.cu", "psc_tiles.cuh", "psc_tiles_lean.cuh", "psc_internal.h"):
         with open(os.path.join(ROOT, "paper_1605_03726_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -447,8 +459,9 @@ def serving_arm(args, local):
     D = [SERVE_D, SERVE_D, 0.0]
     rx = [((0, 1), (2,), SERVE_K)]
     attempts = lambda q: 2000 * (q["counts"][0] + q["counts"][1])   # upper bound: counts fall as C forms
-    # one at a time through the lattice API (a sample of the same replicas)
-    sample = reps[: max(1, args.serial_sample)]
+    # one at a time through the lattice API: by default every replica of the
+    # batched run, so both rates divide the same work
+    sample = reps if args.serial_sample <= 0 else reps[: args.serial_sample]
     t0 = time.perf_counter()
     serial_counts = []
     for q in sample:
@@ -476,6 +489,8 @@ def serving_arm(args, local):
     _, peak = S.memory()
     S.close()
     same = all(np.array_equal(results[i][0], serial_counts[i]) for i in range(len(sample)))
+    sample_attempts = sum(attempts(q) for q in sample)
+    batch_attempts = sum(attempts(q) for q in reps)
     # Poisson arrivals at 200 requests/s (seeded gaps), served as they come
     rnd = random.Random(7)
     arrivals, t = [], 0.0
@@ -505,14 +520,137 @@ def serving_arm(args, local):
                     "2000 hop intervals each" % len(reps),
         "replicas_per_s_batched": round(len(reps) / batch_s, 3),
         "replicas_per_s_serial": round(len(sample) / serial_s, 3),
-        "speedup": round((len(reps) / batch_s) / (len(sample) / serial_s), 2),
-        "serial_sample": len(sample),
+        # rates over the same replica set when the serial run covers all of
+        # them; a partial sample is compared by work (attempt upper bounds)
+        "speedup": round((len(reps) / batch_s) / (len(sample) / serial_s), 2) if len(sample) == len(reps)
+        else round((batch_attempts / batch_s) / (sample_attempts / serial_s), 2),
+        "serial_replicas": len(sample),
+        "same_replica_set": len(sample) == len(reps),
         "serial_matches_batched": bool(same),
+        "serial_matches_batched_replicas": len(sample),
         "batched_attempts_per_s_upper": round(sum(attempts(q) for q in reps) / batch_s, 1),
         "peak_device_bytes": int(peak),
         "poisson_200_per_s": {"p50_s": round(pct(0.50), 4), "p99_s": round(pct(0.99), 4),
                               "replicas_per_s": round(len(reps) / stream_s, 3), "makespan_s": round(stream_s, 3)},
     }
+
+
+# ---------------------------------------------------------------------------
+# the reaction workloads: A + B -> C on 64^3 run to 1000 hop intervals of A;
+# the crowded reversible A + B <-> C on a reflective 256^3 lattice (30 %
+# immobile crowders, A 5 %, B 1 %); the MAPK-like cascade on a periodic 200^3
+# lattice.  Each: attempts/s and us per event on the GPU (CUDA events on the
+# lattice's stream, statistics off), the counted attempts of the same run
+# repeated with statistics on (results are a function of the seed), the
+# one-core oracle on the same model, and the algorithmic bytes of the hop step
+# plus 2 B per collision against the HBM peak (these lattices fit in L2).
+# ---------------------------------------------------------------------------
+def reaction_workloads(args):
+    if ROOT + "/tests" not in sys.path:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import models
+    crowd_events = args.config_events or 650
+    mapk_events = args.config_events or 4000
+    return [
+        dict(name="ab_64cubed", shape=(64, 64, 64), boundary=7, seed=1,
+             recipe=lambda L: models.reaction_diffusion_ab(L, 2000, 2000), until_tau=1000, events=None,
+             workload="64^3 HCP periodic, A and B 2000 each (1 um^2/s), A + B -> C (k = 1e-19 m^3/s, C "
+                      "immobile), run to 1000 hop intervals of A (2000 events)"),
+        dict(name="crowded_256cubed", shape=(256, 256, 256), boundary=0, seed=1,
+             recipe=lambda L: models.crowded_reversible(L, 256 ** 3), until_tau=None, events=crowd_events,
+             workload="256^3 HCP reflective, 30 %% immobile crowders, A 5 %% (5 um^2/s), B 1 %% (1 um^2/s), "
+                      "A + B <-> C (kf = 1e-19 m^3/s, kb = 10 /s; C 0.5 um^2/s); %d events" % crowd_events),
+        dict(name="mapk_200cubed", shape=(200, 200, 200), boundary=7, seed=1,
+             recipe=lambda L: models.mapk_like(L, 5), until_tau=None, events=mapk_events,
+             workload="200^3 HCP periodic, MAPK-like three-tier cascade (22 species, 30 reactions, counts, D "
+                      "and rates drawn from seed 5); %d events" % mapk_events),
+    ]
+
+
+def _reaction_gpu(psc, torch, w, local, stats):
+    stream = torch.cuda.Stream(device=local)
+    L = psc.Lattice(*w["shape"], voxel_radius=RV, boundary=w["boundary"], device=local, stream=stream.cuda_stream)
+    w["recipe"](L)
+    L.populate(w["seed"])
+    if stats:
+        L.set_options(collect_stats=1)
+    L.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    launches0 = L.stats()["launches"]
+    ev0.record(stream)
+    if w["until_tau"]:
+        L.run(w["until_tau"] * L.tau(0))
+    else:
+        L.run_events(w["events"])
+    ev1.record(stream)
+    torch.cuda.synchronize(local)
+    ms = ev0.elapsed_time(ev1)
+    st = L.stats()
+    out = dict(ms=ms, events=L.event_index(), counts=[int(x) for x in L.counts()], stats=st,
+               launches=st["launches"] - launches0)
+    L.close()
+    return out
+
+
+def _reaction_oracle(w, seconds):
+    import oracle
+    t0 = time.perf_counter()
+    L = oracle.Lattice(*w["shape"], RV, w["boundary"], oracle.RULE_SYNC)
+    w["recipe"](L)
+    L.populate(w["seed"])
+    t_pop = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    if w["until_tau"]:
+        tau, t = L.tau(0), 0
+        while t < w["until_tau"] and time.perf_counter() - t1 < seconds:
+            t = min(w["until_tau"], t + 10)
+            L.run(t * tau)
+    else:
+        done = 0
+        while done < w["events"] and time.perf_counter() - t1 < seconds:
+            n = min(w["events"] - done, 10)
+            L.run_events(n)
+            done += n
+    dt = time.perf_counter() - t1
+    att, events = L.stats()["attempts"], L.event_index()
+    L.close()
+    return dict(value=att / dt, events=events, seconds=dt, populate_s=t_pop)
+
+
+def reaction_arm(args, local):
+    import torch
+    import paper_1605_03726_gb300 as psc
+    hbm, peak_kind = peaks()
+    out = {}
+    for w in reaction_workloads(args):
+        _reaction_gpu(psc, torch, w, local, False)                # warm-up (allocations, graphs)
+        run = _reaction_gpu(psc, torch, w, local, False)
+        cnt = _reaction_gpu(psc, torch, w, local, True)
+        assert cnt["counts"] == run["counts"] and cnt["events"] == run["events"]
+        st = cnt["stats"]
+        att = st["attempts"]
+        b_alg = 14.0 * att + 8.0 * st["hops"] + 2.0 * st["collisions"]
+        rate = att / (run["ms"] * 1e-3)
+        entry = {
+            "workload": w["workload"], "attempts_per_s": round(rate, 1), "events": run["events"],
+            "us_per_event": round(run["ms"] * 1e3 / max(1, run["events"]), 3), "ms": round(run["ms"], 3),
+            "attempts": att, "hops": st["hops"], "collisions": st["collisions"], "reactions2": st["reactions2"],
+            "fires": st["fires"], "gpu_launches": int(run["launches"]), "final_counts": run["counts"],
+            "roofline": {"bound": "hbm", "achieved": round(b_alg / (run["ms"] * 1e-3) / 1e9, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(b_alg / (run["ms"] * 1e-3) / 1e9 / hbm, 4),
+                         "bytes_alg": "14 B per attempt + 8 B per hop + 2 B per collision",
+                         "peak_source": peak_kind,
+                         "note": "the lattice state fits in L2, so DRAM is not what bounds these runs"},
+        }
+        if not args.no_cpu_baseline:
+            o = _reaction_oracle(w, min(10.0, args.cpu_seconds))
+            entry["cpu_baseline"] = {
+                "value": round(o["value"], 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d events of the same model and seed after its populate (%.1f s, untimed), single "
+                          "thread, %s" % (o["events"], o["populate_s"], cpu_model())}
+        out[w["name"]] = entry
+    return out
 
 
 # the serving workload on the oracle, one replica per host core
@@ -677,6 +815,8 @@ def main():
         if not args.no_cpu_baseline:
             out["serving"]["cpu_baseline"] = serving_cpu_baseline(args.cpu_seconds,
                                                                   serving_replicas(args.replicas))
+    if world == 1 and not args.no_configs:
+        out["configs"] = reaction_arm(args, local)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args)
     print(json.dumps(out))

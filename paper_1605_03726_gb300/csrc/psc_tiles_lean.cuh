@@ -17,14 +17,20 @@
 //     target next to a wall takes the claim path, which gives the same result);
 //   - the halo refresh indexes the global mirror through per-axis tables of
 //     global brick coordinates instead of per-word wrap arithmetic;
+//   - a contested target whose twelve neighbours all lie in the region can
+//     only be wanted by molecules of this box: its claim goes to a table in
+//     shared memory (lowest id wins, as in the global words) and is read back
+//     inline in the commit phase; targets nearer the region's faces are
+//     claimed in the global words as before;
 //   - hops inside the box update the box (and, for the outermost brick layer,
-//     the global mirror) inline; claim read-backs and departures go to the
-//     deferred queue as before.
+//     the global mirror) inline; global claim read-backs and departures go to
+//     the deferred queue as before.
 
 constexpr uint32_t kLeanOff = 4u | (4u << 11) | (2u << 22);   // region -> box coordinates
 
 struct LeanShared {
     uint32_t* box;
+    unsigned long long* ctab;  // block-local claims: (packed target << 32 | lowest id), all ones = empty
     uint4* tmask;              // [kLeanEntries][2]: masks of the eight-word window
     int32_t* tstep;            // [kLeanEntries]: packed step dx + 2048 dy + 4194304 dz
     int32_t* tbase;            // [kLeanEntries]: first window word minus the mover's word
@@ -42,14 +48,15 @@ __device__ __forceinline__ LeanShared lean_shared(uint32_t* smem, const TilePlan
 {
     LeanShared S;
     S.box = smem;
-    S.tmask = reinterpret_cast<uint4*>(smem + ((P.box_words + 3) & ~3));
+    S.ctab = reinterpret_cast<unsigned long long*>(smem + ((P.box_words + 3) & ~3));
+    S.tmask = reinterpret_cast<uint4*>(S.ctab + (1 << kLeanClaimBits));
     S.tstep = reinterpret_cast<int32_t*>(S.tmask + 2 * kLeanEntries);
     S.tbase = S.tstep + kLeanEntries;
     S.o_t = S.tbase + kLeanEntries;
     S.o_id = reinterpret_cast<uint32_t*>(S.o_t + kTileOutbox);
     S.o_q = S.o_t + 2 * kTileOutbox;
     S.queue = S.o_t + 3 * kTileOutbox;
-    S.hx = S.queue + kTileQueue;
+    S.hx = S.queue + kLeanQueue;
     S.hy = S.hx + b.BI;
     S.hz = S.hy + b.BJ;
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
@@ -237,6 +244,29 @@ __device__ __forceinline__ void lean_depart(const TileArgs& A, const TileBox& b,
     }
 }
 
+// Claim target t (packed box coordinates) for molecule id in the block-local
+// table: linear probing from a hash of t over at most 8 slots.  Returns the
+// slot, or -1 when all 8 hold other targets (the claim then goes to the
+// global words).  Slots only go from empty to a target within an event, so
+// every claimant of t takes the same branch.
+constexpr int kLeanProbes = 8;
+__device__ __forceinline__ int lean_claim_local(unsigned long long* tab, uint32_t t, uint32_t id)
+{
+    const unsigned long long v = ((unsigned long long)t << 32) | id;
+    uint32_t slot = (t * 0x9E3779B1u) >> (32 - kLeanClaimBits);
+    for (int probe = 0; probe < kLeanProbes; ++probe) {
+        const unsigned long long old = atomicCAS(&tab[slot], kEmptySlot, v);
+        if (old == kEmptySlot) return (int)slot;
+        if ((uint32_t)(old >> 32) == t) {
+            atomicMin(&tab[slot], v);
+            return (int)slot;
+        }
+        slot = (slot + 1u) & ((1u << kLeanClaimBits) - 1u);
+    }
+    return -1;
+}
+constexpr uint32_t kLeanLocal = 0x20000000u;   // claimed in the local table (slot in bits 4-13)
+
 // global voxel index of packed box coordinates t (a target next to the region)
 __device__ __forceinline__ int32_t lean_voxel(const Geometry& G, const TileBox& b, uint32_t t)
 {
@@ -244,6 +274,84 @@ __device__ __forceinline__ int32_t lean_voxel(const Geometry& G, const TileBox& 
     uint64_t wr;
     tile_global(G, b, (int)(t & 0x7FFu), (int)((t >> 11) & 0x7FFu), (int)(t >> 22), i, j, k, wr);
     return i + G.ni * (j + G.nj * k);
+}
+
+// End of a phase: once the whole block is done, publish flags[r] = value and
+// wait until every neighbouring box (up to 26, across periodic wraps) has
+// published at least value.  Two block barriers in all.  Bounded like the
+// grid barrier; false (error raised) on time-out.  *s_ok is 1 from the launch
+// on and becomes 0 only on a time-out, after which the kernel returns.
+__device__ __forceinline__ bool lean_phase_sync(const TileArgs& A, uint32_t* flags, int r, uint32_t value,
+                                                int* s_ok)
+{
+    const TilePlan& P = A.plan;
+    const uint32_t bf = A.ev.geo.bflags;
+    const uint32_t target = value + (A.barrier_phantom ? 0x40000000u : 0u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&flags[r], value);
+    }
+    if (threadIdx.x < 27 && threadIdx.x != 13) {
+        int ri = r % P.pi + (int)(threadIdx.x % 3) - 1;
+        int rj = (r / P.pi) % P.pj + (int)((threadIdx.x / 3) % 3) - 1;
+        int rk = r / (P.pi * P.pj) + (int)(threadIdx.x / 9) - 1;
+        bool skip = false;
+        if (ri < 0 || ri >= P.pi) { if (bf & 1u) ri = (ri + P.pi) % P.pi; else skip = true; }
+        if (rj < 0 || rj >= P.pj) { if (bf & 2u) rj = (rj + P.pj) % P.pj; else skip = true; }
+        if (rk < 0 || rk >= P.pk) { if (bf & 4u) rk = (rk + P.pk) % P.pk; else skip = true; }
+        if (!skip) {
+            const volatile uint32_t* f = flags + (rk * P.pj + rj) * P.pi + ri;
+            uint64_t t0 = 0;
+            for (unsigned int spins = 0; *f < target; ++spins) {
+                if ((spins & 1023u) == 0u) {
+                    const uint64_t now = globaltimer_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > A.barrier_timeout_ns || spins >= kBarrierMaxSpins) {
+                        atomicOr(&A.ev.sc->err, kErrBarrierTimeout);
+                        *s_ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Start of an event (after the neighbours' commits): the arrivals of the last
+// event join the box and the bucket buffer `buf`, and (refresh) the halo is
+// read again from the global mirror, in one pass with one block barrier.  The
+// inbox count is reset afterwards by thread 0; senders write the inbox again
+// only after this box publishes its next claim phase.
+__device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const TileBox& b, const LeanShared& S, int& n,
+                                            int buf, bool refresh, const FastDiv& div_bi, const FastDiv& div_bj2)
+{
+    const int cap = A.plan.cap;
+    const int m = min(*((volatile int32_t*)&A.in_cnt[r]), cap);
+    const int64_t base = (int64_t)r * cap;
+    for (int x = threadIdx.x; x < m; x += blockDim.x) {
+        const int32_t t = __ldcg(&A.in_vox[base + x]);
+        const uint32_t id = __ldcg(&A.in_ids[base + x]);
+        int32_t i, j, k;
+        decode(A.ev.geo, (uint32_t)t, i, j, k);
+        int w;
+        uint32_t mk;
+        tile_local(b, i, j, k, w, mk);
+        atomicOr(&S.box[w], mk);
+        if (n + x < cap) {
+            A.b_vox[buf][base + n + x] = (int32_t)tile_pack(i - 4 * b.bi0, j - 4 * b.bj0, k - 2 * b.bk0);
+            A.b_ids[buf][base + n + x] = id;
+        } else {
+            atomicOr(&A.ev.sc->err, kErrListOverflow);
+        }
+    }
+    if (refresh) lean_refresh_halo(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false);
+    __syncthreads();
+    if (threadIdx.x == 0) A.in_cnt[r] = 0;
+    n = min(n + m, cap);
 }
 
 // Claim-phase decision: bits 0-3 the direction, kTileMove (no claim needed)
@@ -271,6 +379,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
     constexpr int U = 2;                                 // molecules whose memory operations go out together
     tile_build_owners(P, S.own);
     lean_build_tables(b, P, G, S);
+    for (int q = threadIdx.x; q < (1 << kLeanClaimBits); q += blockDim.x) S.ctab[q] = kEmptySlot;
+    if (threadIdx.x == 0) s_misc[3] = 1;
     __syncthreads();
     // region words from the global mirror, then the halo
     for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
@@ -293,13 +403,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         const int32_t* bv = A.b_vox[cur] + base;
         const uint32_t* bi = A.b_ids[cur] + base;
         uint32_t* bs = A.b_state + base;
-        if (e > 0) {
-            // the neighbours' last commits: halo bits, arrivals, reset claim words
-            if (!tile_wait_neighbours(A, A.done, r, (uint32_t)e, &s_misc[3])) return;
-            tile_ingest(A, r, b, box, n, cur, s_misc);
-            lean_refresh_halo(P, b, S, div_bi, div_bj2, a.bits, false);
-            __syncthreads();
-        }
+        if (e > 0) lean_ingest(A, r, b, S, n, cur, true, div_bi, div_bj2);   // after the neighbours' commits
         // ---- claim phase ----
         for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
             uint32_t vv[U], ii[U];
@@ -331,8 +435,16 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                     const uint32_t t = p + (uint32_t)S.tstep[e12];
                     if (!(box[lean_word(t, BI, BIJ)] & (1u << lean_place(t)))) {
                         // vacant, but other molecules can reach it: the lowest id wins
-                        atomicMin(&claim[lean_voxel(G, b, t)], ii[u]);
-                        st |= kTileClaimed;
+                        int slot = -1;
+                        if (((t & 0x7FFu) - 5u) < rxn - 2u && (((t >> 11) & 0x7FFu) - 5u) < ryn - 2u &&
+                            ((t >> 22) - 3u) < rzn - 2u)
+                            slot = lean_claim_local(S.ctab, t, ii[u]);   // all its neighbours are ours
+                        if (slot >= 0) {
+                            st |= kLeanLocal | ((uint32_t)slot << 4);
+                        } else {
+                            atomicMin(&claim[lean_voxel(G, b, t)], ii[u]);
+                            st |= kTileClaimed;
+                        }
                     }
                 }
                 bs[xm] = st;
@@ -345,8 +457,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
             s_misc[5] = 0;
         }
         // a claim word is touched only by boxes that are all neighbours of each other
-        tile_publish(A.claimed, r, (uint32_t)(e + 1));
-        if (!tile_wait_neighbours(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;
+        if (!lean_phase_sync(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;
         // ---- commit phase: hops inside the region here, everything else queued ----
         int32_t* ov = A.b_vox[cur ^ 1] + base;
         uint32_t* oi = A.b_ids[cur ^ 1] + base;
@@ -366,7 +477,17 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                 uint32_t w = vv[u];
                 bool keep = xm < n;
                 bool defer = (st & kTileClaimed) != 0u;
-                if (st & kTileMove) {
+                if (st & kLeanLocal) {
+                    // block-local claim: an interior target, the move stays in the region
+                    if ((uint32_t)S.ctab[(st >> 4) & ((1u << kLeanClaimBits) - 1u)] == ii[u]) {
+                        const uint32_t p = w + kLeanOff;
+                        const uint32_t c = lean_place(p);
+                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
+                        lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
+                        w = t - kLeanOff;
+                        ++n_hop;
+                    }
+                } else if (st & kTileMove) {
                     const uint32_t p = w + kLeanOff;
                     const uint32_t c = lean_place(p);
                     const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
@@ -380,7 +501,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                 }
                 if (defer) {
                     const int k = atomicAdd(&s_misc[5], 1);
-                    if (k < kTileQueue) {
+                    if (k < kLeanQueue) {
                         S.queue[k] = xm;
                         keep = false;
                     } else {
@@ -413,7 +534,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         __syncthreads();
         {
             // queued molecules: claim read-backs of a batch in flight together
-            const int m = min(s_misc[5], kTileQueue);
+            const int m = min(s_misc[5], kLeanQueue);
             for (int c0 = 0; c0 < m; c0 += U * blockDim.x) {
                 int32_t xx[U], tv[U];
                 uint32_t vv[U], ii[U], ss[U], rb[U];
@@ -465,6 +586,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         }
         __syncthreads();
         n = s_misc[1];
+        // every read-back of the local table is done: empty it for the next event
+        for (int q = threadIdx.x; q < (1 << kLeanClaimBits); q += blockDim.x) S.ctab[q] = kEmptySlot;
         // the outbox to the inboxes of the boxes the molecules entered
         {
             const int m = min(s_misc[2], kTileOutbox);
@@ -479,12 +602,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                 }
             }
         }
-        tile_publish(A.done, r, (uint32_t)(e + 1));
+        // halo bits, arrivals and reset claim words of every neighbour are out
+        if (!lean_phase_sync(A, A.done, r, (uint32_t)(e + 1), &s_misc[3])) return;
     }
     // the last event's arrivals, then the region's bits back to the mirror
-    if (A.n_events > 0 && !tile_wait_neighbours(A, A.done, r, (uint32_t)A.n_events, &s_misc[3])) return;
-    if (A.n_events > 0) tile_ingest(A, r, b, box, n, A.n_events & 1, s_misc);
-    __syncthreads();
+    if (A.n_events > 0) lean_ingest(A, r, b, S, n, A.n_events & 1, false, div_bi, div_bj2);
     for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
         const int wx = 1 + q % b.ei, wy = 1 + (q / b.ei) % b.ej, wz = 1 + q / (b.ei * b.ej);
         a.bits[tile_region_word(P, b, wx, wy, wz)] = box[(wz * b.BJ + wy) * BI + wx];

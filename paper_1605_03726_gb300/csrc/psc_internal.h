@@ -276,12 +276,12 @@ inline int tile_smem_bytes(const TilePlan& P)
 // direction), per-axis halo tables, plus the areas of the general kernel
 constexpr int kLeanEntries = 32 * 12;
 constexpr int kLeanClaimBits = 10;          // block-local claim table: 2^10 slots of 8 bytes
-constexpr int kLeanQueue = 512;             // deferred molecules (global claims, departures)
+constexpr int kLeanOutbox = 512;            // departures staged per event (more go straight to the inboxes)
 inline int lean_smem_bytes(const TilePlan& P)
 {
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
     return ((P.box_words + 3) & ~3) * 4 + (8 << kLeanClaimBits) + kLeanEntries * 8 * 4 + kLeanEntries * 2 * 4 +
-           kTileOutbox * 12 + kLeanQueue * 4 + halo_tables * 4 + ((P.nbi + P.nbj + P.nbk + 15) & ~15);
+           kLeanOutbox * 12 + halo_tables * 4 + ((P.nbi + P.nbj + P.nbk + 15) & ~15);
 }
 constexpr int kTileThreads = 512;
 constexpr int kTileBlocksPerSM = 2;

@@ -22,9 +22,10 @@
 //     shared memory (lowest id wins, as in the global words) and is read back
 //     inline in the commit phase; targets nearer the region's faces are
 //     claimed in the global words as before;
-//   - hops inside the box update the box (and, for the outermost brick layer,
-//     the global mirror) inline; global claim read-backs and departures go to
-//     the deferred queue as before.
+//   - the commit phase handles every molecule in one pass: hops inside the
+//     box update the box (and, for the outermost brick layer, the global
+//     mirror), global claim words are read back in batches of loads, and
+//     departures go to the outbox, with no deferred queue.
 
 constexpr uint32_t kLeanOff = 4u | (4u << 11) | (2u << 22);   // region -> box coordinates
 
@@ -37,7 +38,6 @@ struct LeanShared {
     int32_t* o_t;              // outbox: departures of an event
     uint32_t* o_id;
     int32_t* o_q;
-    int32_t* queue;            // bucket slots whose handling is deferred
     int32_t* hx;               // global brick coordinate of box word coordinate x (-1: wall)
     int32_t* hy;
     int32_t* hz;
@@ -53,10 +53,9 @@ __device__ __forceinline__ LeanShared lean_shared(uint32_t* smem, const TilePlan
     S.tstep = reinterpret_cast<int32_t*>(S.tmask + 2 * kLeanEntries);
     S.tbase = S.tstep + kLeanEntries;
     S.o_t = S.tbase + kLeanEntries;
-    S.o_id = reinterpret_cast<uint32_t*>(S.o_t + kTileOutbox);
-    S.o_q = S.o_t + 2 * kTileOutbox;
-    S.queue = S.o_t + 3 * kTileOutbox;
-    S.hx = S.queue + kLeanQueue;
+    S.o_id = reinterpret_cast<uint32_t*>(S.o_t + kLeanOutbox);
+    S.o_q = S.o_t + 2 * kLeanOutbox;
+    S.hx = S.o_t + 3 * kLeanOutbox;
     S.hy = S.hx + b.BI;
     S.hz = S.hy + b.BJ;
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
@@ -130,56 +129,78 @@ __device__ void lean_build_tables(const TileBox& b, const TilePlan& P, const Geo
 // Refresh the halo (box words outside the region) from the global mirror;
 // words behind a reflective wall are all ones.  Halo word q: first the two
 // z faces (full planes), then the full rows of the two y faces, then the end
-// words of the other rows; each thread issues its loads in groups of eight.
-__device__ __forceinline__ void lean_refresh_halo(const TilePlan& P, const TileBox& b, const LeanShared& S,
-                                                  const FastDiv& div_bi, const FastDiv& div_bj2,
-                                                  const uint32_t* bits, bool initial)
+// words of the other rows; each thread takes the words q0 + h * blockDim.x,
+// h < kLeanHalo, of a chunk, whose loads go out together.
+constexpr int kLeanHalo = 8;
+
+__device__ __forceinline__ int lean_halo_total(const TileBox& b)
+{
+    return 2 * b.BI * b.BJ + 2 * (b.BK - 2) * b.BI + 2 * (b.BK - 2) * (b.BJ - 2);
+}
+
+__device__ __forceinline__ void lean_halo_load(const TilePlan& P, const TileBox& b, const LeanShared& S,
+                                               const FastDiv& div_bi, const FastDiv& div_bj2, const uint32_t* bits,
+                                               bool initial, int q0, int (&idx)[kLeanHalo],
+                                               uint32_t (&val)[kLeanHalo])
 {
     const int BI = b.BI, BJ = b.BJ, BK = b.BK, BIJ = BI * BJ;
     const int n_z = 2 * BIJ;
     const int n_y = n_z + 2 * (BK - 2) * BI;
     const int total = n_y + 2 * (BK - 2) * (BJ - 2);
-    constexpr int H = 8;
-    for (int q0 = threadIdx.x; q0 < total; q0 += H * blockDim.x) {
-        int idx[H];
-        uint32_t val[H];
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-            const int q = q0 + h * blockDim.x;
-            idx[h] = -1;
-            val[h] = ~0u;
-            if (q >= total) continue;
-            int wx, wy, wz;
-            if (q < n_z) {
-                const int f = q >= BIJ ? 1 : 0;
-                const int r = q - f * BIJ;
-                wy = (int)fdiv((uint32_t)r, div_bi);
-                wx = r - wy * BI;
-                wz = f ? BK - 1 : 0;
-            } else if (q < n_y) {
-                const int r2 = q - n_z;
-                const int row = (int)fdiv((uint32_t)r2, div_bi);
-                wx = r2 - row * BI;
-                wz = 1 + (row >> 1);
-                wy = (row & 1) ? BJ - 1 : 0;
-            } else {
-                const int r3 = q - n_y;
-                const int col = (int)fdiv((uint32_t)r3, div_bj2);
-                wy = 1 + r3 - col * (BJ - 2);
-                wz = 1 + (col >> 1);
-                wx = (col & 1) ? BI - 1 : 0;
-            }
-            const int gi = S.hx[wx], gj = S.hy[wy], gk = S.hz[wz];
-            idx[h] = (wz * BJ + wy) * BI + wx;
-            if ((gi | gj | gk) >= 0) {
-                val[h] = __ldcg(&bits[((int64_t)gk * P.nbj + gj) * P.nbi + gi]);
-            } else if (!initial) {
-                idx[h] = -1;              // walls never change
-            }
+    for (int h = 0; h < kLeanHalo; ++h) {
+        const int q = q0 + h * blockDim.x;
+        idx[h] = -1;
+        val[h] = ~0u;
+        if (q >= total) continue;
+        int wx, wy, wz;
+        if (q < n_z) {
+            const int f = q >= BIJ ? 1 : 0;
+            const int r = q - f * BIJ;
+            wy = (int)fdiv((uint32_t)r, div_bi);
+            wx = r - wy * BI;
+            wz = f ? BK - 1 : 0;
+        } else if (q < n_y) {
+            const int r2 = q - n_z;
+            const int row = (int)fdiv((uint32_t)r2, div_bi);
+            wx = r2 - row * BI;
+            wz = 1 + (row >> 1);
+            wy = (row & 1) ? BJ - 1 : 0;
+        } else {
+            const int r3 = q - n_y;
+            const int col = (int)fdiv((uint32_t)r3, div_bj2);
+            wy = 1 + r3 - col * (BJ - 2);
+            wz = 1 + (col >> 1);
+            wx = (col & 1) ? BI - 1 : 0;
         }
+        const int gi = S.hx[wx], gj = S.hy[wy], gk = S.hz[wz];
+        idx[h] = (wz * BJ + wy) * BI + wx;
+        if ((gi | gj | gk) >= 0) {
+            val[h] = __ldcg(&bits[((int64_t)gk * P.nbj + gj) * P.nbi + gi]);
+        } else if (!initial) {
+            idx[h] = -1;                  // walls never change
+        }
+    }
+}
+
+__device__ __forceinline__ void lean_halo_store(const LeanShared& S, const int (&idx)[kLeanHalo],
+                                                const uint32_t (&val)[kLeanHalo])
+{
 #pragma unroll
-        for (int h = 0; h < H; ++h)
-            if (idx[h] >= 0) S.box[idx[h]] = val[h];
+    for (int h = 0; h < kLeanHalo; ++h)
+        if (idx[h] >= 0) S.box[idx[h]] = val[h];
+}
+
+__device__ __forceinline__ void lean_refresh_halo(const TilePlan& P, const TileBox& b, const LeanShared& S,
+                                                  const FastDiv& div_bi, const FastDiv& div_bj2,
+                                                  const uint32_t* bits, bool initial)
+{
+    const int total = lean_halo_total(b);
+    for (int q0 = threadIdx.x; q0 < total; q0 += kLeanHalo * blockDim.x) {
+        int idx[kLeanHalo];
+        uint32_t val[kLeanHalo];
+        lean_halo_load(P, b, S, div_bi, div_bj2, bits, initial, q0, idx, val);
+        lean_halo_store(S, idx, val);
     }
 }
 
@@ -228,7 +249,7 @@ __device__ __forceinline__ void lean_depart(const TileArgs& A, const TileBox& b,
     const int q = tile_region_of(A.plan, S.own, gi, gj, gk);
     const int32_t tv = gi + G.ni * (gj + G.nj * gk);
     const int o = atomicAdd(s_out_n, 1);
-    if (o < kTileOutbox) {
+    if (o < kLeanOutbox) {
         S.o_t[o] = tv;
         S.o_id[o] = id;
         S.o_q[o] = q;
@@ -332,6 +353,11 @@ __device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const Tile
     const int cap = A.plan.cap;
     const int m = min(*((volatile int32_t*)&A.in_cnt[r]), cap);
     const int64_t base = (int64_t)r * cap;
+    // the first chunk of halo loads goes out before the arrivals are read
+    const int total = refresh ? lean_halo_total(b) : 0;
+    int idx[kLeanHalo];
+    uint32_t val[kLeanHalo];
+    if (refresh) lean_halo_load(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false, threadIdx.x, idx, val);
     for (int x = threadIdx.x; x < m; x += blockDim.x) {
         const int32_t t = __ldcg(&A.in_vox[base + x]);
         const uint32_t id = __ldcg(&A.in_ids[base + x]);
@@ -348,7 +374,13 @@ __device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const Tile
             atomicOr(&A.ev.sc->err, kErrListOverflow);
         }
     }
-    if (refresh) lean_refresh_halo(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false);
+    if (refresh) {
+        lean_halo_store(S, idx, val);
+        for (int q0 = threadIdx.x + kLeanHalo * blockDim.x; q0 < total; q0 += kLeanHalo * blockDim.x) {
+            lean_halo_load(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false, q0, idx, val);
+            lean_halo_store(S, idx, val);
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) A.in_cnt[r] = 0;
     n = min(n + m, cap);
@@ -458,11 +490,12 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         }
         // a claim word is touched only by boxes that are all neighbours of each other
         if (!lean_phase_sync(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;
-        // ---- commit phase: hops inside the region here, everything else queued ----
+        // ---- commit phase: every molecule in one pass ----
         int32_t* ov = A.b_vox[cur ^ 1] + base;
         uint32_t* oi = A.b_ids[cur ^ 1] + base;
         for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
-            uint32_t vv[U], ii[U], ss[U];
+            uint32_t vv[U], ii[U], ss[U], tt[U], rb[U];
+            int32_t tv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int x = c0 + u * blockDim.x + threadIdx.x;
@@ -470,118 +503,44 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                 ii[u] = x < n ? __ldcg(bi + x) : 0u;
                 ss[u] = x < n ? __ldcg(bs + x) : 0u;
             }
+            // targets; the global claim words of contested targets near the faces go out together
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t p = vv[u] + kLeanOff;
+                tt[u] = p + (uint32_t)S.tstep[lean_place(p) * 12u + (ss[u] & 15u)];
+                tv[u] = -1;
+                rb[u] = 0u;
+                if (ss[u] & kTileClaimed) {
+                    tv[u] = lean_voxel(G, b, tt[u]);
+                    rb[u] = __ldcg(&claim[tv[u]]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int xm = c0 + u * blockDim.x + threadIdx.x;
                 const uint32_t st = ss[u];
                 uint32_t w = vv[u];
                 bool keep = xm < n;
-                bool defer = (st & kTileClaimed) != 0u;
+                bool win = (st & kTileMove) != 0u;
                 if (st & kLeanLocal) {
-                    // block-local claim: an interior target, the move stays in the region
-                    if ((uint32_t)S.ctab[(st >> 4) & ((1u << kLeanClaimBits) - 1u)] == ii[u]) {
-                        const uint32_t p = w + kLeanOff;
-                        const uint32_t c = lean_place(p);
-                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
-                        lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
-                        w = t - kLeanOff;
-                        ++n_hop;
-                    }
-                } else if (st & kTileMove) {
-                    const uint32_t p = w + kLeanOff;
+                    win = (uint32_t)S.ctab[(st >> 4) & ((1u << kLeanClaimBits) - 1u)] == ii[u];
+                } else if ((st & kTileClaimed) && rb[u] == ii[u]) {
+                    win = true;
+                    claim[tv[u]] = kNoClaim;             // the winner resets the word
+                }
+                if (keep && win) {
+                    const uint32_t p = w + kLeanOff, t = tt[u];
                     const uint32_t c = lean_place(p);
-                    const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
+                    ++n_hop;
                     if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn && ((t >> 22) - 2u) < rzn) {
                         lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
                         w = t - kLeanOff;
-                        ++n_hop;
                     } else {
-                        defer = true;
-                    }
-                }
-                if (defer) {
-                    const int k = atomicAdd(&s_misc[5], 1);
-                    if (k < kLeanQueue) {
-                        S.queue[k] = xm;
+                        lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
                         keep = false;
-                    } else {
-                        // queue full: handle it here
-                        const uint32_t p = w + kLeanOff;
-                        const uint32_t c = lean_place(p);
-                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
-                        bool win = (st & kTileMove) != 0u;
-                        if (!win) {
-                            const int32_t tv = lean_voxel(G, b, t);
-                            win = __ldcg(&claim[tv]) == ii[u];
-                            if (win) claim[tv] = kNoClaim;
-                        }
-                        if (win) {
-                            ++n_hop;
-                            if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn &&
-                                ((t >> 22) - 2u) < rzn) {
-                                lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
-                                w = t - kLeanOff;
-                            } else {
-                                lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
-                                keep = false;
-                            }
-                        }
                     }
                 }
                 tile_keep(keep, w, ii[u], &s_misc[1], ov, oi);
-            }
-        }
-        __syncthreads();
-        {
-            // queued molecules: claim read-backs of a batch in flight together
-            const int m = min(s_misc[5], kLeanQueue);
-            for (int c0 = 0; c0 < m; c0 += U * blockDim.x) {
-                int32_t xx[U], tv[U];
-                uint32_t vv[U], ii[U], ss[U], rb[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int k = c0 + u * blockDim.x + threadIdx.x;
-                    xx[u] = k < m ? S.queue[k] : -1;
-                    vv[u] = xx[u] >= 0 ? (uint32_t)__ldcg(bv + xx[u]) : 0u;
-                    ii[u] = xx[u] >= 0 ? __ldcg(bi + xx[u]) : 0u;
-                    ss[u] = xx[u] >= 0 ? __ldcg(bs + xx[u]) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    rb[u] = 0u;
-                    tv[u] = -1;
-                    if (!(ss[u] & kTileClaimed)) continue;
-                    const uint32_t p = vv[u] + kLeanOff;
-                    const uint32_t t = p + (uint32_t)S.tstep[lean_place(p) * 12u + (ss[u] & 15u)];
-                    tv[u] = lean_voxel(G, b, t);
-                    rb[u] = __ldcg(&claim[tv[u]]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t st = ss[u];
-                    uint32_t w = vv[u];
-                    bool keep = xx[u] >= 0;
-                    bool win = (st & kTileMove) != 0u;
-                    if ((st & kTileClaimed) && rb[u] == ii[u]) {
-                        win = true;
-                        claim[tv[u]] = kNoClaim;         // the winner resets the word
-                    }
-                    if (keep && win) {
-                        const uint32_t p = w + kLeanOff;
-                        const uint32_t c = lean_place(p);
-                        const uint32_t t = p + (uint32_t)S.tstep[c * 12u + (st & 15u)];
-                        ++n_hop;
-                        if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn &&
-                            ((t >> 22) - 2u) < rzn) {
-                            lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
-                            w = t - kLeanOff;
-                        } else {
-                            lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
-                            keep = false;
-                        }
-                    }
-                    tile_keep(keep, w, ii[u], &s_misc[1], ov, oi);
-                }
             }
         }
         __syncthreads();
@@ -590,7 +549,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         for (int q = threadIdx.x; q < (1 << kLeanClaimBits); q += blockDim.x) S.ctab[q] = kEmptySlot;
         // the outbox to the inboxes of the boxes the molecules entered
         {
-            const int m = min(s_misc[2], kTileOutbox);
+            const int m = min(s_misc[2], kLeanOutbox);
             for (int o = threadIdx.x; o < m; o += blockDim.x) {
                 const int q = S.o_q[o];
                 const int slot = atomicAdd(&A.in_cnt[q], 1);

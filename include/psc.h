@@ -469,6 +469,70 @@ int  psc_server_memory(const psc_server *S, int64_t *bytes_in_use, int64_t *peak
 void psc_server_destroy(psc_server *S);
 
 /*
+ * Slabs: the lattice split along k into sub-domains, each with a ghost layer on
+ * either side refreshed from its neighbours at every event (the paper's
+ * sub-domains with ghost voxels, Sec. 2.5), for events of one species without
+ * reactions under the synchronous rule.  Slab `index` of `count` owns the
+ * layers index * m .. index * m + m - 1, m = nk / count (nk a multiple of
+ * count, m >= 2).  An event takes three calls with an exchange with both
+ * neighbouring slabs after each of the first two:
+ *   psc_slab_claim    directions drawn, vacant targets claimed (lowest id);
+ *                     send_claim[0] / [1] hold the claims on the two layers
+ *                     at the lower / upper face (a target there can be
+ *                     wanted from both sides);
+ *   psc_slab_commit   recv_claim[0] / [1] (the neighbours' send_claim[1] /
+ *                     [0]) are merged, winners move; send_commit[side] holds
+ *                     the molecules that entered that neighbour's layers and
+ *                     this slab's boundary layer on that side;
+ *   psc_slab_apply    recv_commit[0] / [1] (the neighbours' send_commit[1] /
+ *                     [0]) refresh the ghost layers and add the arrivals.
+ * Side 0 is the lower neighbour (index - 1), side 1 the upper one (index + 1);
+ * along a periodic k axis slab 0 and slab count - 1 are neighbours (with one
+ * slab, the slab is its own neighbour), along a reflective one the outer
+ * sides exchange nothing.  Results are bit-identical to psc_run_events on the
+ * whole lattice (same seed and event indices).
+ *
+ *   psc_slab_create   from a populated lattice L: its only mobile species is
+ *                     `species`, which has no reactions (others immobile,
+ *                     else PSC_E_UNSUPPORTED; HCP only); copies the slab's
+ *                     share of L's molecules and occupancy and L's event
+ *                     index; device and cuda_stream (NULL: a stream the slab
+ *                     owns) for the slab's state.  L stays as it was.
+ *   psc_slab_buffers_get / _set   the eight exchange buffers (device memory
+ *                     of claim_bytes or commit_bytes each) the slab allocated,
+ *                     or ones the caller provides instead (e.g. buffers a
+ *                     collective library sends and receives); the caller
+ *                     keeps ownership of buffers it sets.
+ *   psc_slabs_run_events   n_events events of slabs[0 .. count - 1] (all of
+ *                     one split, index order) in this process, exchanging
+ *                     by device copies (peer copies across devices).
+ *   psc_slab_coords   the slab's molecules: global (i, j, k) into ijk[3 a],
+ *                     ids, unwrapped positions as psc_unwrapped (xyz may be
+ *                     NULL), in list order; *n_out = count (cap = 0 sizes).
+ *   psc_slab_synchronize  waits; reports PSC_E_CAPACITY if a list or a
+ *                     message overflowed.
+ * Errors: PSC_E_ARG, PSC_E_ORDER (L not populated), PSC_E_DIMS,
+ * PSC_E_UNSUPPORTED, PSC_E_NOMEM, PSC_E_CAPACITY, PSC_E_LIMIT, PSC_E_CUDA.
+ */
+typedef struct psc_slab psc_slab;
+typedef struct {
+    void *send_claim[2], *recv_claim[2], *send_commit[2], *recv_commit[2];
+} psc_slab_buffers;
+int  psc_slab_create(psc_slab **out, psc_lattice *L, int32_t species, int32_t index, int32_t count,
+                     int device, void *cuda_stream);
+int  psc_slab_buffers_get(const psc_slab *S, psc_slab_buffers *b, int64_t *claim_bytes,
+                          int64_t *commit_bytes);
+int  psc_slab_buffers_set(psc_slab *S, const psc_slab_buffers *b);
+int  psc_slab_claim(psc_slab *S);
+int  psc_slab_commit(psc_slab *S);
+int  psc_slab_apply(psc_slab *S);
+int  psc_slabs_run_events(psc_slab **slabs, int32_t count, int64_t n_events);
+int  psc_slab_synchronize(psc_slab *S);
+int  psc_slab_coords(psc_slab *S, int32_t *ijk, uint32_t *ids, int32_t *xyz, int64_t cap, int64_t *n_out);
+int  psc_slab_event_index(const psc_slab *S, uint32_t *g);
+void psc_slab_destroy(psc_slab *S);
+
+/*
  * psc_hop_events_static -- n_events diffusion events of one species that has
  * no reactions, on molecule buffers the caller owns, without allocating any
  * memory.  (The paper has no counterpart: this is a deployment variant of

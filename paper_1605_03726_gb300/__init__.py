@@ -40,6 +40,12 @@ class Options(ctypes.Structure):
         "tile_regions", "subvolume", "tile_lean")]
 
 
+class SlabBuffers(ctypes.Structure):
+    """psc_slab_buffers: device pointers, [0] the lower side, [1] the upper side."""
+    _fields_ = [("send_claim", ctypes.c_void_p * 2), ("recv_claim", ctypes.c_void_p * 2),
+                ("send_commit", ctypes.c_void_p * 2), ("recv_commit", ctypes.c_void_p * 2)]
+
+
 class KernelTimes(ctypes.Structure):
     _fields_ = [("claim_ms", ctypes.c_double), ("commit_ms", ctypes.c_double),
                 ("reconcile_ms", ctypes.c_double), ("resort_ms", ctypes.c_double),
@@ -143,6 +149,18 @@ def lib():
             "psc_server_result": (ctypes.c_int, [P, i64, P, i32, ctypes.POINTER(dbl)]),
             "psc_server_memory": (ctypes.c_int, [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "psc_server_destroy": (None, [P]),
+            "psc_slab_create": (ctypes.c_int, [ctypes.POINTER(P), P, i32, i32, i32, ctypes.c_int, P]),
+            "psc_slab_buffers_get": (ctypes.c_int, [P, ctypes.POINTER(SlabBuffers), ctypes.POINTER(i64),
+                                                    ctypes.POINTER(i64)]),
+            "psc_slab_buffers_set": (ctypes.c_int, [P, ctypes.POINTER(SlabBuffers)]),
+            "psc_slab_claim": (ctypes.c_int, [P]),
+            "psc_slab_commit": (ctypes.c_int, [P]),
+            "psc_slab_apply": (ctypes.c_int, [P]),
+            "psc_slabs_run_events": (ctypes.c_int, [ctypes.POINTER(P), i32, i64]),
+            "psc_slab_synchronize": (ctypes.c_int, [P]),
+            "psc_slab_coords": (ctypes.c_int, [P, P, P, P, i64, ctypes.POINTER(i64)]),
+            "psc_slab_event_index": (ctypes.c_int, [P, ctypes.POINTER(u32)]),
+            "psc_slab_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -161,7 +179,9 @@ EXPORTED = ("psc_lattice_create", "psc_add_species", "psc_add_reaction", "psc_se
             "psc_hop_events_static", "psc_batch_create", "psc_batch_add", "psc_batch_remove", "psc_batch_size",
             "psc_batch_run_events", "psc_batch_run", "psc_batch_launches", "psc_batch_destroy",
             "psc_server_create", "psc_server_submit", "psc_server_step", "psc_server_result", "psc_server_memory",
-            "psc_server_destroy")
+            "psc_server_destroy", "psc_slab_create", "psc_slab_buffers_get", "psc_slab_buffers_set",
+            "psc_slab_claim", "psc_slab_commit", "psc_slab_apply", "psc_slabs_run_events", "psc_slab_synchronize",
+            "psc_slab_coords", "psc_slab_event_index", "psc_slab_destroy")
 
 
 class EngineError(RuntimeError):
@@ -449,3 +469,135 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Slab:
+    """One slab of a lattice split along k (psc_slab_*): created from a
+    populated Lattice, advanced either together with the other slabs of the
+    split in this process (run_slabs) or one per rank through claim / commit /
+    apply with the exchanges in between (SlabRanks)."""
+
+    def __init__(self, lattice, species, index, count, device=0, stream=None):
+        self._h = ctypes.c_void_p()
+        _check("psc_slab_create", lib().psc_slab_create(ctypes.byref(self._h), lattice._h, species, index, count,
+                                                        device, ctypes.c_void_p(stream) if stream else None))
+        self.index, self.count = index, count
+
+    def close(self):
+        if self._h:
+            lib().psc_slab_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def buffers(self):
+        b = SlabBuffers()
+        cb, mb = ctypes.c_int64(), ctypes.c_int64()
+        _check("psc_slab_buffers_get", lib().psc_slab_buffers_get(self._h, ctypes.byref(b), ctypes.byref(cb),
+                                                                  ctypes.byref(mb)))
+        return b, cb.value, mb.value
+
+    def set_buffers(self, send_claim, recv_claim, send_commit, recv_commit):
+        """Exchange buffers the caller owns (device pointers, two each: lower, upper side)."""
+        b = SlabBuffers()
+        for name, ptrs in (("send_claim", send_claim), ("recv_claim", recv_claim),
+                           ("send_commit", send_commit), ("recv_commit", recv_commit)):
+            arr = getattr(b, name)
+            arr[0], arr[1] = int(ptrs[0]), int(ptrs[1])
+        _check("psc_slab_buffers_set", lib().psc_slab_buffers_set(self._h, ctypes.byref(b)))
+
+    def claim(self):
+        _check("psc_slab_claim", lib().psc_slab_claim(self._h))
+
+    def commit(self):
+        _check("psc_slab_commit", lib().psc_slab_commit(self._h))
+
+    def apply(self):
+        _check("psc_slab_apply", lib().psc_slab_apply(self._h))
+
+    def synchronize(self):
+        _check("psc_slab_synchronize", lib().psc_slab_synchronize(self._h))
+
+    def event_index(self):
+        g = ctypes.c_uint32()
+        _check("psc_slab_event_index", lib().psc_slab_event_index(self._h, ctypes.byref(g)))
+        return g.value
+
+    def coords(self):
+        """(ijk, ids, xyz) of the slab's molecules: global coordinates, ids and
+        unwrapped positions, in list order."""
+        n = ctypes.c_int64()
+        _check("psc_slab_coords", lib().psc_slab_coords(self._h, None, None, None, 0, ctypes.byref(n)))
+        m = max(1, n.value)
+        ijk = np.zeros((m, 3), dtype=np.int32)
+        ids = np.zeros(m, dtype=np.uint32)
+        xyz = np.zeros((m, 3), dtype=np.int32)
+        _check("psc_slab_coords", lib().psc_slab_coords(self._h, _ptr(ijk), _ptr(ids), _ptr(xyz), m,
+                                                        ctypes.byref(n)))
+        return ijk[: n.value], ids[: n.value], xyz[: n.value]
+
+
+def run_slabs(slabs, n_events):
+    """n_events events of all slabs of a split held by this process."""
+    arr = (ctypes.c_void_p * len(slabs))(*[s._h.value for s in slabs])
+    _check("psc_slabs_run_events", lib().psc_slabs_run_events(arr, len(slabs), int(n_events)))
+
+
+def slab_neighbour(rank, world, side, periodic_k):
+    """Rank holding the neighbouring slab on `side` (0 below, 1 above), None at a wall."""
+    q = rank - 1 if side == 0 else rank + 1
+    if 0 <= q < world:
+        return q
+    return (q % world) if periodic_k else None
+
+
+class SlabRanks:
+    """Host side of a split with one slab per rank: the neighbour ranks and the
+    two exchanges of every event as point-to-point sends and receives of whole
+    buffers through torch.distributed.  A slab's send[1] (its upper face) goes
+    to the upper neighbour's recv[0]; its send[0] to the lower neighbour's
+    recv[1].  Every rank posts the upward traffic first, then the downward
+    traffic, so that messages between one pair of ranks match in order (as
+    NCCL requires) even when the two neighbours are the same rank."""
+
+    UP, DOWN = 0, 1
+
+    def __init__(self, rank, world, periodic_k):
+        self.rank, self.world, self.periodic_k = rank, world, bool(periodic_k)
+        self.nb = [slab_neighbour(rank, world, s, periodic_k) for s in (0, 1)]
+
+    def exchange(self, send, recv):
+        """send[side] to the neighbour on that side, recv[side] from it (tensors)."""
+        import torch.distributed as dist
+        if self.world == 1:
+            if self.periodic_k:
+                recv[0].copy_(send[1])
+                recv[1].copy_(send[0])
+            return
+        ops = []
+        if self.nb[1] is not None:
+            ops.append(dist.P2POp(dist.isend, send[1], self.nb[1], tag=self.UP))
+        if self.nb[0] is not None:
+            ops.append(dist.P2POp(dist.irecv, recv[0], self.nb[0], tag=self.UP))
+        if self.nb[0] is not None:
+            ops.append(dist.P2POp(dist.isend, send[0], self.nb[0], tag=self.DOWN))
+        if self.nb[1] is not None:
+            ops.append(dist.P2POp(dist.irecv, recv[1], self.nb[1], tag=self.DOWN))
+        if ops:
+            for req in dist.batch_isend_irecv(ops):
+                req.wait()
+
+    def run_events(self, slab, bufs, n_events):
+        """n_events events of this rank's slab; bufs = dict of the slab's
+        exchange tensors (send_claim, recv_claim, send_commit, recv_commit,
+        each a pair) already set with Slab.set_buffers."""
+        for _ in range(int(n_events)):
+            slab.claim()
+            self.exchange(bufs["send_claim"], bufs["recv_claim"])
+            slab.commit()
+            self.exchange(bufs["send_commit"], bufs["recv_commit"])
+            slab.apply()

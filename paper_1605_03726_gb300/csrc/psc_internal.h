@@ -340,6 +340,39 @@ void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesL
 void launch_mirror_from_list_checked(uint32_t* bits, const Geometry& geo, const SpeciesList& list,
                                      const int32_t* count, int64_t V, int32_t* err, int blocks, cudaStream_t st);
 
+// ---- slabs along k with ghost layers (psc_slab.cuh, psc_slab.cpp) ----
+struct SlabEntry {                 // a molecule handed to a neighbouring slab
+    int32_t i, j, k;               // global coordinates of the voxel it entered
+    uint32_t id;
+    uint64_t img;                  // packed wrap counters
+};
+
+struct SlabArgs {
+    int32_t ni, nj, nk, m, k0;     // global extents, owned layers, first owned layer
+    uint32_t bflags;
+    uint32_t lw;                   // words per layer of the bit array (layers start on words)
+    uint32_t* bits;                // (m + 2) * lw words: bit i + ni j of layer L, set = occupied or wall
+    uint32_t* claim;               // (m + 2) * ni * nj words, kNoClaim when free
+    int32_t* vox[2];               // molecule lists by buffer: local voxel i + ni (j + nj L)
+    uint32_t* ids[2];
+    uint64_t* img[2];
+    int32_t* count;                // [2] molecules per buffer
+    int32_t cap;
+    int32_t cur;                   // buffer holding the molecules at the start of the event
+    uint8_t* dec;                  // claim-phase decision per molecule
+    uint8_t* send_commit[2];       // [0] to the lower neighbour, [1] to the upper one
+    const uint8_t* recv_commit[2];
+    const uint32_t* recv_claim[2];
+    int32_t tcap;                  // entries a commit message holds
+    int32_t has[2];                // a neighbour on that side (else a wall)
+    int32_t* err;
+    uint32_t key0, key1, g, s;     // Philox key, event index, species
+};
+
+void launch_slab_claim(const SlabArgs& A, int blocks, cudaStream_t st);
+void launch_slab_commit(const SlabArgs& A, int blocks, cudaStream_t st);
+void launch_slab_apply(const SlabArgs& A, int blocks, cudaStream_t st);
+
 // ---- batched launches: many lattices (replicas) per launch ----
 // Item x covers blocks [block0, next block0) of the launch and runs the event
 // (or list) `sel` of replica `rep` with event index g.  Argument templates of

@@ -1510,6 +1510,7 @@ void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStrea
 }
 
 #include "psc_tiles.cuh"
+#include "psc_slab.cuh"
 #include "psc_subvol.cuh"
 
 }  // namespace psc

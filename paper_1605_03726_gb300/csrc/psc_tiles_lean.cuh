@@ -436,14 +436,23 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         const uint32_t* bi = A.b_ids[cur] + base;
         uint32_t* bs = A.b_state + base;
         if (e > 0) lean_ingest(A, r, b, S, n, cur, true, div_bi, div_bj2);   // after the neighbours' commits
-        // ---- claim phase ----
+        // ---- claim phase (the next chunk's bucket entries load while one is processed) ----
+        uint32_t pv[U], pi_[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int x = u * blockDim.x + threadIdx.x;
+            pv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+            pi_[u] = x < n ? __ldcg(bi + x) : 0u;
+        }
         for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
             uint32_t vv[U], ii[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int x = c0 + u * blockDim.x + threadIdx.x;
-                vv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
-                ii[u] = x < n ? __ldcg(bi + x) : 0u;
+                vv[u] = pv[u];
+                ii[u] = pi_[u];
+                const int x = c0 + (U + u) * blockDim.x + threadIdx.x;
+                pv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+                pi_[u] = x < n ? __ldcg(bi + x) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -493,15 +502,26 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         // ---- commit phase: every molecule in one pass ----
         int32_t* ov = A.b_vox[cur ^ 1] + base;
         uint32_t* oi = A.b_ids[cur ^ 1] + base;
+        uint32_t qv[U], qi[U], qs[U];             // the next chunk, loading ahead
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int x = u * blockDim.x + threadIdx.x;
+            qv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+            qi[u] = x < n ? __ldcg(bi + x) : 0u;
+            qs[u] = x < n ? __ldcg(bs + x) : 0u;
+        }
         for (int c0 = 0; c0 < n; c0 += U * blockDim.x) {
             uint32_t vv[U], ii[U], ss[U], tt[U], rb[U];
             int32_t tv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int x = c0 + u * blockDim.x + threadIdx.x;
-                vv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
-                ii[u] = x < n ? __ldcg(bi + x) : 0u;
-                ss[u] = x < n ? __ldcg(bs + x) : 0u;
+                vv[u] = qv[u];
+                ii[u] = qi[u];
+                ss[u] = qs[u];
+                const int x = c0 + (U + u) * blockDim.x + threadIdx.x;
+                qv[u] = x < n ? (uint32_t)__ldcg(bv + x) : 0u;
+                qi[u] = x < n ? __ldcg(bi + x) : 0u;
+                qs[u] = x < n ? __ldcg(bs + x) : 0u;
             }
             // targets; the global claim words of contested targets near the faces go out together
 #pragma unroll

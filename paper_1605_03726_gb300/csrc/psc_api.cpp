@@ -424,6 +424,13 @@ static int tile_buffers(psc_lattice* L, const TilePlan& P, int64_t ids)
         if (!T.claim) return PSC_E_NOMEM;
         launch_fill_u32(T.claim, kNoClaim, (size_t)L->V, L->sm_count * 8, L->stream);
     }
+    if (P.lean && (int64_t)P.regions * lean_halo_cap(P) > T.halo_entries) {
+        if (T.halo_tab) dev_free_one(L, T.halo_tab);
+        const int64_t ne = (int64_t)P.regions * lean_halo_cap(P);
+        T.halo_tab = (uint2*)dev_alloc(L, (size_t)ne * sizeof(uint2));
+        T.halo_entries = T.halo_tab ? ne : 0;
+        if (!T.halo_tab) return PSC_E_NOMEM;
+    }
     if (ids > T.ids) {
         if (T.img_id) dev_free_one(L, T.img_id);
         T.img_id = (uint64_t*)dev_alloc(L, (size_t)ids * 8);
@@ -465,6 +472,8 @@ int enqueue_tiles(psc_lattice* L, int s, int64_t n_events, const TilePlan& P)
     A.in_ids = L->tile.in_ids;
     A.in_cnt = L->tile.in_cnt;
     A.img_id = L->tile.img_id;
+    A.halo_tab = L->tile.halo_tab;
+    A.halo_cap = P.lean ? (int32_t)lean_halo_cap(P) : 0;
     A.id_lo = (uint32_t)id_lo;
     A.n_events = (int32_t)n_events;
     A.barrier = L->barrier;
@@ -1632,7 +1641,7 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
     b += L->subvol.subvols * 8 + L->subvol.slots * 17 + (L->subvol.counters ? 128 : 0);
     // tile kernel buffers, once a stretch has used them
     const auto& T = L->tile;
-    b += T.slots * 4 * 5 + (int64_t)T.regions * 4 * 4 + T.ids * 8;
+    b += T.slots * 4 * 5 + (int64_t)T.regions * 4 * 4 + T.ids * 8 + T.halo_entries * (int64_t)sizeof(uint2);
     if (T.claim) b += L->V * 4;
     *bytes = b;
     return PSC_OK;

@@ -211,6 +211,8 @@ struct TileArgs {
     uint32_t* in_ids;
     int32_t* in_cnt;           // [regions]
     uint64_t* img_id;          // wrap counters by id - id_lo
+    uint2* halo_tab;           // lean kernel: [regions][halo_cap] (box word, global word or ~0 behind a wall)
+    int32_t halo_cap;
     uint32_t id_lo;
     int32_t n_events;
     BarrierState* barrier;
@@ -279,6 +281,12 @@ inline int tile_smem_bytes(const TilePlan& P)
 constexpr int kLeanEntries = 32 * 12;
 constexpr int kLeanClaimBits = 10;          // block-local claim table: 2^10 slots of 8 bytes
 constexpr int kLeanOutbox = 512;            // departures staged per event (more go straight to the inboxes)
+// halo words of the largest box of a plan (the lean kernel's per-box halo table)
+inline int64_t lean_halo_cap(const TilePlan& P)
+{
+    const int64_t BI = P.ei + 2, BJ = P.ej + 2, BK = P.ek + 2;
+    return 2 * BI * BJ + 2 * (BK - 2) * BI + 2 * (BK - 2) * (BJ - 2);
+}
 inline int lean_smem_bytes(const TilePlan& P)
 {
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;

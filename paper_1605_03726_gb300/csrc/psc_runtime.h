@@ -133,6 +133,8 @@ struct psc_lattice {
         uint32_t* done = nullptr;
         uint64_t* img_id = nullptr;
         uint32_t* claim = nullptr;     // per-voxel claim words when the lattice has none
+        uint2* halo_tab = nullptr;     // lean kernel: halo word table per box
+        int64_t halo_entries = 0;
     } tile;
     int tile_smem = -1;                // shared memory a tile block may use (-1: not queried yet)
 

@@ -15,8 +15,9 @@
 //   - words behind a reflective wall hold all ones in the box, so no hop
 //     needs a bounds test (a wall voxel looks occupied: the hop fails, and a
 //     target next to a wall takes the claim path, which gives the same result);
-//   - the halo refresh indexes the global mirror through per-axis tables of
-//     global brick coordinates instead of per-word wrap arithmetic;
+//   - the halo refresh reads a per-box table of (box word, global word) pairs
+//     built once per launch from per-axis tables of global brick coordinates,
+//     instead of per-word wrap arithmetic at every event;
 //   - a contested target whose twelve neighbours all lie in the region can
 //     only be wanted by molecules of this box: its claim goes to a table in
 //     shared memory (lowest id wins, as in the global words) and is read back
@@ -126,82 +127,91 @@ __device__ void lean_build_tables(const TileBox& b, const TilePlan& P, const Geo
     }
 }
 
-// Refresh the halo (box words outside the region) from the global mirror;
-// words behind a reflective wall are all ones.  Halo word q: first the two
-// z faces (full planes), then the full rows of the two y faces, then the end
-// words of the other rows; each thread takes the words q0 + h * blockDim.x,
-// h < kLeanHalo, of a chunk, whose loads go out together.
+// The halo (box words outside the region) is refreshed from the global
+// mirror at every event; words behind a reflective wall are all ones and never
+// change.  Halo word q: first the two z faces (full planes), then the full rows
+// of the two y faces, then the end words of the other rows.  Each block writes
+// the (box word, global word) pair of every halo word into its part of a table
+// once per launch; an event then reads its pairs instead of recomputing them.
+// A thread takes the words q0 + h * blockDim.x, h < kLeanHalo, of a chunk, whose
+// loads go out together.
 constexpr int kLeanHalo = 8;
+constexpr uint32_t kLeanWall = ~0u;         // global word of a halo word behind a wall
 
 __device__ __forceinline__ int lean_halo_total(const TileBox& b)
 {
     return 2 * b.BI * b.BJ + 2 * (b.BK - 2) * b.BI + 2 * (b.BK - 2) * (b.BJ - 2);
 }
 
-__device__ __forceinline__ void lean_halo_load(const TilePlan& P, const TileBox& b, const LeanShared& S,
-                                               const FastDiv& div_bi, const FastDiv& div_bj2, const uint32_t* bits,
-                                               bool initial, int q0, int (&idx)[kLeanHalo],
-                                               uint32_t (&val)[kLeanHalo])
+// (box word, global word or kLeanWall) of halo word q
+__device__ __forceinline__ uint2 lean_halo_pair(const TilePlan& P, const TileBox& b, const LeanShared& S,
+                                                const FastDiv& div_bi, const FastDiv& div_bj2, int q)
 {
     const int BI = b.BI, BJ = b.BJ, BK = b.BK, BIJ = BI * BJ;
     const int n_z = 2 * BIJ;
     const int n_y = n_z + 2 * (BK - 2) * BI;
-    const int total = n_y + 2 * (BK - 2) * (BJ - 2);
-#pragma unroll
-    for (int h = 0; h < kLeanHalo; ++h) {
-        const int q = q0 + h * blockDim.x;
-        idx[h] = -1;
-        val[h] = ~0u;
-        if (q >= total) continue;
-        int wx, wy, wz;
-        if (q < n_z) {
-            const int f = q >= BIJ ? 1 : 0;
-            const int r = q - f * BIJ;
-            wy = (int)fdiv((uint32_t)r, div_bi);
-            wx = r - wy * BI;
-            wz = f ? BK - 1 : 0;
-        } else if (q < n_y) {
-            const int r2 = q - n_z;
-            const int row = (int)fdiv((uint32_t)r2, div_bi);
-            wx = r2 - row * BI;
-            wz = 1 + (row >> 1);
-            wy = (row & 1) ? BJ - 1 : 0;
-        } else {
-            const int r3 = q - n_y;
-            const int col = (int)fdiv((uint32_t)r3, div_bj2);
-            wy = 1 + r3 - col * (BJ - 2);
-            wz = 1 + (col >> 1);
-            wx = (col & 1) ? BI - 1 : 0;
-        }
-        const int gi = S.hx[wx], gj = S.hy[wy], gk = S.hz[wz];
-        idx[h] = (wz * BJ + wy) * BI + wx;
-        if ((gi | gj | gk) >= 0) {
-            val[h] = __ldcg(&bits[((int64_t)gk * P.nbj + gj) * P.nbi + gi]);
-        } else if (!initial) {
-            idx[h] = -1;                  // walls never change
-        }
+    int wx, wy, wz;
+    if (q < n_z) {
+        const int f = q >= BIJ ? 1 : 0;
+        const int r = q - f * BIJ;
+        wy = (int)fdiv((uint32_t)r, div_bi);
+        wx = r - wy * BI;
+        wz = f ? BK - 1 : 0;
+    } else if (q < n_y) {
+        const int r2 = q - n_z;
+        const int row = (int)fdiv((uint32_t)r2, div_bi);
+        wx = r2 - row * BI;
+        wz = 1 + (row >> 1);
+        wy = (row & 1) ? BJ - 1 : 0;
+    } else {
+        const int r3 = q - n_y;
+        const int col = (int)fdiv((uint32_t)r3, div_bj2);
+        wy = 1 + r3 - col * (BJ - 2);
+        wz = 1 + (col >> 1);
+        wx = (col & 1) ? BI - 1 : 0;
+    }
+    const int gi = S.hx[wx], gj = S.hy[wy], gk = S.hz[wz];
+    const uint32_t g = (gi | gj | gk) >= 0 ? (uint32_t)(((int64_t)gk * P.nbj + gj) * P.nbi + gi) : kLeanWall;
+    return make_uint2((uint32_t)((wz * BJ + wy) * BI + wx), g);
+}
+
+// Launch prologue: the block's table, and every halo word (walls included)
+__device__ __forceinline__ void lean_halo_init(const TileArgs& A, int r, const TileBox& b, const LeanShared& S,
+                                               const FastDiv& div_bi, const FastDiv& div_bj2)
+{
+    const int total = lean_halo_total(b);
+    uint2* tab = A.halo_tab + (int64_t)r * A.halo_cap;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const uint2 e = lean_halo_pair(A.plan, b, S, div_bi, div_bj2, q);
+        tab[q] = e;                       // read back only by this thread (same q stride)
+        S.box[e.x] = e.y == kLeanWall ? ~0u : __ldcg(&A.ev.bits[e.y]);
     }
 }
 
-__device__ __forceinline__ void lean_halo_store(const LeanShared& S, const int (&idx)[kLeanHalo],
+// the table entries of chunk q0 (kLeanWall pairs past the end)
+__device__ __forceinline__ void lean_halo_fetch(const TileArgs& A, int r, int total, int q0, uint2 (&e)[kLeanHalo])
+{
+    const uint2* tab = A.halo_tab + (int64_t)r * A.halo_cap;
+#pragma unroll
+    for (int h = 0; h < kLeanHalo; ++h) {
+        const int q = q0 + h * blockDim.x;
+        e[h] = q < total ? __ldcg(reinterpret_cast<const uint2*>(tab) + q) : make_uint2(0u, kLeanWall);
+    }
+}
+
+__device__ __forceinline__ void lean_halo_load(const uint32_t* bits, const uint2 (&e)[kLeanHalo],
+                                               uint32_t (&val)[kLeanHalo])
+{
+#pragma unroll
+    for (int h = 0; h < kLeanHalo; ++h) val[h] = e[h].y != kLeanWall ? __ldcg(&bits[e[h].y]) : 0u;
+}
+
+__device__ __forceinline__ void lean_halo_store(const LeanShared& S, const uint2 (&e)[kLeanHalo],
                                                 const uint32_t (&val)[kLeanHalo])
 {
 #pragma unroll
     for (int h = 0; h < kLeanHalo; ++h)
-        if (idx[h] >= 0) S.box[idx[h]] = val[h];
-}
-
-__device__ __forceinline__ void lean_refresh_halo(const TilePlan& P, const TileBox& b, const LeanShared& S,
-                                                  const FastDiv& div_bi, const FastDiv& div_bj2,
-                                                  const uint32_t* bits, bool initial)
-{
-    const int total = lean_halo_total(b);
-    for (int q0 = threadIdx.x; q0 < total; q0 += kLeanHalo * blockDim.x) {
-        int idx[kLeanHalo];
-        uint32_t val[kLeanHalo];
-        lean_halo_load(P, b, S, div_bi, div_bj2, bits, initial, q0, idx, val);
-        lean_halo_store(S, idx, val);
-    }
+        if (e[h].y != kLeanWall) S.box[e[h].x] = val[h];
 }
 
 // A molecule of the box (packed box coordinates p, place c) moves to packed
@@ -348,16 +358,15 @@ __device__ __forceinline__ bool lean_phase_sync(const TileArgs& A, uint32_t* fla
 // inbox count is reset afterwards by thread 0; senders write the inbox again
 // only after this box publishes its next claim phase.
 __device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const TileBox& b, const LeanShared& S, int& n,
-                                            int buf, bool refresh, const FastDiv& div_bi, const FastDiv& div_bj2)
+                                            int buf, bool refresh, const uint2 (&first)[kLeanHalo])
 {
     const int cap = A.plan.cap;
     const int m = min(*((volatile int32_t*)&A.in_cnt[r]), cap);
     const int64_t base = (int64_t)r * cap;
     // the first chunk of halo loads goes out before the arrivals are read
     const int total = refresh ? lean_halo_total(b) : 0;
-    int idx[kLeanHalo];
     uint32_t val[kLeanHalo];
-    if (refresh) lean_halo_load(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false, threadIdx.x, idx, val);
+    if (refresh) lean_halo_load(A.ev.bits, first, val);
     for (int x = threadIdx.x; x < m; x += blockDim.x) {
         const int32_t t = __ldcg(&A.in_vox[base + x]);
         const uint32_t id = __ldcg(&A.in_ids[base + x]);
@@ -375,10 +384,12 @@ __device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const Tile
         }
     }
     if (refresh) {
-        lean_halo_store(S, idx, val);
+        lean_halo_store(S, first, val);
         for (int q0 = threadIdx.x + kLeanHalo * blockDim.x; q0 < total; q0 += kLeanHalo * blockDim.x) {
-            lean_halo_load(A.plan, b, S, div_bi, div_bj2, A.ev.bits, false, q0, idx, val);
-            lean_halo_store(S, idx, val);
+            uint2 e[kLeanHalo];
+            lean_halo_fetch(A, r, total, q0, e);
+            lean_halo_load(A.ev.bits, e, val);
+            lean_halo_store(S, e, val);
         }
     }
     __syncthreads();
@@ -419,7 +430,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         const int wx = 1 + q % b.ei, wy = 1 + (q / b.ei) % b.ej, wz = 1 + q / (b.ei * b.ej);
         box[(wz * b.BJ + wy) * BI + wx] = __ldcg(&a.bits[tile_region_word(P, b, wx, wy, wz)]);
     }
-    lean_refresh_halo(P, b, S, div_bi, div_bj2, a.bits, true);
+    lean_halo_init(A, r, b, S, div_bi, div_bj2);
+    const int halo_total = lean_halo_total(b);
     int n = *((volatile int32_t*)&A.b_cnt[r]);
     // the scatter left voxel indices: store coordinates relative to the region
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
@@ -428,6 +440,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         A.b_vox[0][base + x] = (int32_t)tile_pack(i - 4 * b.bi0, j - 4 * b.bj0, k - 2 * b.bk0);
     }
     unsigned long long n_att = 0, n_hop = 0;
+    uint2 halo_first[kLeanHalo];
     __syncthreads();
     for (int e = 0; e < A.n_events; ++e) {
         const uint32_t g = a.g + (uint32_t)e;
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         const int32_t* bv = A.b_vox[cur] + base;
         const uint32_t* bi = A.b_ids[cur] + base;
         uint32_t* bs = A.b_state + base;
-        if (e > 0) lean_ingest(A, r, b, S, n, cur, true, div_bi, div_bj2);   // after the neighbours' commits
+        if (e > 0) lean_ingest(A, r, b, S, n, cur, true, halo_first);   // after the neighbours' commits
         // ---- claim phase (the next chunk's bucket entries load while one is processed) ----
         uint32_t pv[U], pi_[U];
 #pragma unroll
@@ -581,11 +594,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                 }
             }
         }
+        // the first chunk of the next halo refresh: its table entries load during the wait
+        lean_halo_fetch(A, r, halo_total, threadIdx.x, halo_first);
         // halo bits, arrivals and reset claim words of every neighbour are out
         if (!lean_phase_sync(A, A.done, r, (uint32_t)(e + 1), &s_misc[3])) return;
     }
     // the last event's arrivals, then the region's bits back to the mirror
-    if (A.n_events > 0) lean_ingest(A, r, b, S, n, A.n_events & 1, false, div_bi, div_bj2);
+    if (A.n_events > 0) lean_ingest(A, r, b, S, n, A.n_events & 1, false, halo_first);
     for (int q = threadIdx.x; q < b.ei * b.ej * b.ek; q += blockDim.x) {
         const int wx = 1 + q % b.ei, wy = 1 + (q / b.ei) % b.ej, wz = 1 + q / (b.ei * b.ej);
         a.bits[tile_region_word(P, b, wx, wy, wz)] = box[(wz * b.BJ + wy) * BI + wx];

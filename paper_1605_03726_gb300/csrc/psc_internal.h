@@ -291,7 +291,8 @@ inline int lean_smem_bytes(const TilePlan& P)
 {
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
     return ((P.box_words + 3) & ~3) * 4 + (8 << kLeanClaimBits) + kLeanEntries * 8 * 4 + kLeanEntries * 2 * 4 +
-           kLeanOutbox * 12 + halo_tables * 4 + ((P.nbi + P.nbj + P.nbk + 15) & ~15);
+           kLeanOutbox * 12 + halo_tables * 4 + ((P.box_words + 31) >> 5) * 4 +
+           ((P.nbi + P.nbj + P.nbk + 15) & ~15);
 }
 constexpr int kTileThreads = 512;
 constexpr int kTileBlocksPerSM = 2;

@@ -42,6 +42,7 @@ struct LeanShared {
     int32_t* hx;               // global brick coordinate of box word coordinate x (-1: wall)
     int32_t* hy;
     int32_t* hz;
+    uint32_t* obits;           // bit w: box word w is in the region's outermost brick layer
     uint8_t* own;              // owner tables
 };
 
@@ -60,7 +61,8 @@ __device__ __forceinline__ LeanShared lean_shared(uint32_t* smem, const TilePlan
     S.hy = S.hx + b.BI;
     S.hz = S.hy + b.BJ;
     const int halo_tables = ((P.ei + 2) + (P.ej + 2) + (P.ek + 2) + 3) & ~3;
-    S.own = reinterpret_cast<uint8_t*>(S.hx + halo_tables);
+    S.obits = reinterpret_cast<uint32_t*>(S.hx + halo_tables);
+    S.own = reinterpret_cast<uint8_t*>(S.obits + ((P.box_words + 31) >> 5));
     return S;
 }
 
@@ -72,15 +74,6 @@ __device__ __forceinline__ int lean_word(uint32_t p, int BI, int BIJ)
 __device__ __forceinline__ uint32_t lean_place(uint32_t p)
 {
     return (p & 3u) | ((p >> 9) & 0xCu) | ((p >> 18) & 0x10u);
-}
-
-// Is the box word of packed coordinates p in the region's outermost brick
-// layer (read by neighbouring boxes as halo)?  p must lie in the region.
-__device__ __forceinline__ bool lean_outer(uint32_t p, const TileBox& b)
-{
-    const uint32_t wx = (p >> 2) & 0x1FFu, wy = (p >> 13) & 0x1FFu, wz = p >> 23;
-    return (wx - 2u) >= (uint32_t)(b.ei - 2) || (wy - 2u) >= (uint32_t)(b.ej - 2) ||
-           (wz - 2u) >= (uint32_t)(b.ek - 2);
 }
 
 // global mirror word of the region word holding packed coordinates p
@@ -217,12 +210,12 @@ __device__ __forceinline__ void lean_halo_store(const LeanShared& S, const uint2
 // A molecule of the box (packed box coordinates p, place c) moves to packed
 // box coordinates t inside its region: box bits, and the global mirror for
 // words of the outermost layer.
-__device__ __forceinline__ void lean_move_inside(const TileArgs& A, const TileBox& b, uint32_t* box, int BI, int BIJ,
-                                                 int64_t gbase, uint32_t p, uint32_t c, uint32_t t)
+__device__ __forceinline__ void lean_move_inside(const TileArgs& A, const LeanShared& S, uint32_t* box, int BI,
+                                                 int BIJ, int64_t gbase, uint32_t p, uint32_t c, uint32_t t)
 {
     const int wv = lean_word(p, BI, BIJ), wt = lean_word(t, BI, BIJ);
     const uint32_t mv = 1u << c, mt = 1u << lean_place(t);
-    const bool vo = lean_outer(p, b), to = lean_outer(t, b);
+    const bool vo = (S.obits[wv >> 5] >> (wv & 31)) & 1u, to = (S.obits[wt >> 5] >> (wt & 31)) & 1u;
     if (wv == wt) {
         atomicXor(&box[wv], mv | mt);
         if (vo) atomicXor(&A.ev.bits[lean_gword(p, A.plan, gbase)], mv | mt);
@@ -423,6 +416,18 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
     tile_build_owners(P, S.own);
     lean_build_tables(b, P, G, S);
     for (int q = threadIdx.x; q < (1 << kLeanClaimBits); q += blockDim.x) S.ctab[q] = kEmptySlot;
+    for (int q = threadIdx.x; q < (P.box_words + 31) >> 5; q += blockDim.x) {
+        uint32_t m = 0u;
+        for (int z = 0; z < 32; ++z) {
+            const int w = q * 32 + z;
+            if (w >= b.BI * b.BJ * b.BK) break;
+            const int wx = w % b.BI, wy = (w / b.BI) % b.BJ, wz = w / (b.BI * b.BJ);
+            const bool inside = wx >= 1 && wx <= b.ei && wy >= 1 && wy <= b.ej && wz >= 1 && wz <= b.ek;
+            const bool outer = wx == 1 || wx == b.ei || wy == 1 || wy == b.ej || wz == 1 || wz == b.ek;
+            if (inside && outer) m |= 1u << z;
+        }
+        S.obits[q] = m;
+    }
     if (threadIdx.x == 0) s_misc[3] = 1;
     __syncthreads();
     // region words from the global mirror, then the halo
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
                     const uint32_t c = lean_place(p);
                     ++n_hop;
                     if (((t & 0x7FFu) - 4u) < rxn && (((t >> 11) & 0x7FFu) - 4u) < ryn && ((t >> 22) - 2u) < rzn) {
-                        lean_move_inside(A, b, box, BI, BIJ, gbase, p, c, t);
+                        lean_move_inside(A, S, box, BI, BIJ, gbase, p, c, t);
                         w = t - kLeanOff;
                     } else {
                         lean_depart(A, b, S, BI, BIJ, gbase, &s_misc[2], p, c, t, ii[u]);
@@ -582,15 +587,26 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         for (int q = threadIdx.x; q < (1 << kLeanClaimBits); q += blockDim.x) S.ctab[q] = kEmptySlot;
         // the outbox to the inboxes of the boxes the molecules entered
         {
+            // one inbox atomic per destination box and warp
             const int m = min(s_misc[2], kLeanOutbox);
-            for (int o = threadIdx.x; o < m; o += blockDim.x) {
-                const int q = S.o_q[o];
-                const int slot = atomicAdd(&A.in_cnt[q], 1);
-                if (slot < cap) {
-                    A.in_vox[(int64_t)q * cap + slot] = S.o_t[o];
-                    A.in_ids[(int64_t)q * cap + slot] = S.o_id[o];
-                } else {
-                    atomicOr(&a.sc->err, kErrListOverflow);
+            for (int o0 = threadIdx.x & ~31; o0 < m; o0 += blockDim.x) {
+                const int o = o0 + (threadIdx.x & 31);
+                const bool has = o < m;
+                const int q = has ? S.o_q[o] : -1;
+                const unsigned peers = __match_any_sync(0xFFFFFFFFu, q);
+                const int leader = __ffs(peers) - 1;
+                const int lane = threadIdx.x & 31;
+                int base0 = 0;
+                if (has && lane == leader) base0 = atomicAdd(&A.in_cnt[q], __popc(peers));
+                base0 = __shfl_sync(0xFFFFFFFFu, base0, leader);
+                if (has) {
+                    const int slot = base0 + __popc(peers & ((1u << lane) - 1u));
+                    if (slot < cap) {
+                        A.in_vox[(int64_t)q * cap + slot] = S.o_t[o];
+                        A.in_ids[(int64_t)q * cap + slot] = S.o_id[o];
+                    } else {
+                        atomicOr(&a.sc->err, kErrListOverflow);
+                    }
                 }
             }
         }

@@ -348,7 +348,9 @@ def gpu_arm(args, rank, world, local):
     t_event_ms = hop_ms / n_ev
     achieved = b_alg * N_MOL / (t_event_ms * 1e-3) / 1e9
     tiles_used = kt.get("tile_launches", 0) > 0
-    tr = profiled_traffic("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
+    lean_used = kt.get("tile_lean_events", 0) > 0
+    prof_name = "tile_lean_512cubed" if lean_used else ("tile_run_512cubed" if tiles_used else "hop_run_512cubed")
+    tr = profiled_traffic(prof_name)
     traffic = None
     events_per_launch = kt["run_events"] / max(1, kt["run_launches"]) if persistent else 1
     if persistent and args.rule == "sync" and args.compartments == "none" and args.lattice == "hcp" and tr and tr.get("kernel_rev") == kernel_revision() and \
@@ -357,8 +359,7 @@ def gpu_arm(args, rank, world, local):
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
         "frac": round(achieved / hbm, 4), "traffic": traffic,
-        "traffic_unit": "DRAM bytes per launch (ncu, profiles/%s.md)" % ("tile_run_512cubed" if tiles_used
-                                                                          else "hop_run_512cubed"),
+        "traffic_unit": "DRAM bytes per launch (ncu, profiles/%s.md)" % prof_name,
         "events_per_launch": events_per_launch,
         "bytes_alg_per_launch": round(b_alg * N_MOL * events_per_launch),
         "kernel": ("k_subvol_run (sub-volume rule: eight colour passes per event, rounds per colour)"

@@ -229,7 +229,7 @@ int enqueue_event(psc_lattice* L, int s)
         const ReconcileArgs r = reconcile_args(L, x);
         const int rb = event_blocks(L, L->cap[x]);
         launch_reconcile(r, rb, threads, L->stream);
-        launch_fill_multi(r, std::min(rb, 64), L->stream);
+        launch_fill(r, L->stream);
         L->launches += 2;
     }
     if (L->fo2[s]) {

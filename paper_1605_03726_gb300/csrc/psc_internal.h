@@ -109,8 +109,6 @@ struct Scalars {
     int32_t births;                  // births queued in the current event
     int32_t err;                     // kErr* bits
     uint32_t g_base;                 // index of the first event of a replayed graph
-    int32_t fill_cursor;             // multi-block fill: next leaver slot to hand out
-    int32_t fill_done;               // multi-block fill: blocks finished
     unsigned long long stats[kNumStats];
 };
 
@@ -327,8 +325,6 @@ void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t*
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
 // the list's leavers' slots filled from its tail (one block)
 void launch_fill(const ReconcileArgs& r, cudaStream_t st);
-// the same over many blocks (single lattices)
-void launch_fill_multi(const ReconcileArgs& r, int blocks, cudaStream_t st);
 void launch_births(const EventArgs& a, cudaStream_t st);
 void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
 // molecule r (ids in species order, species s owning [offsets[s],

@@ -1039,55 +1039,6 @@ __global__ void __launch_bounds__(1024) k_fill(const ReconcileArgs r)
     fill_body(r);
 }
 
-// Many blocks: every survivor at or above the new length n - k takes one hole
-// below it.  Holes are handed out through a cursor over the leavers' slots
-// (tmp.vox), skipping leavers that lie at or above the new length; as there
-// are exactly as many holes as such survivors, each survivor gets one.  The
-// last block to finish sets the new length and rewinds the counters (every
-// block read the old length before it: it started before the last one ended).
-__global__ void __launch_bounds__(256) k_fill_multi(const ReconcileArgs r)
-{
-    const int32_t n = r.sc->counts[r.x];
-    const int32_t k = min(r.sc->tmp_count[r.x], n);
-    const int32_t n2 = n - k;
-    if (k > 0) {
-        for (int p = n2 + blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-            if (r.list.vox[p] < 0) continue;                // it left
-            int32_t h = -1;
-            for (;;) {
-                const int q = atomicAdd(&r.sc->fill_cursor, 1);
-                if (q >= k) {
-                    atomicOr(&r.sc->err, kErrListOverflow);
-                    break;
-                }
-                const int32_t c = r.tmp.vox[q];
-                if (c < n2) {
-                    h = c;
-                    break;
-                }
-            }
-            if (h < 0) continue;
-            r.list.vox[h] = r.list.vox[p];
-            r.list.ids[h] = r.list.ids[p];
-            r.list.img[h] = r.list.img[p];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&r.sc->fill_done, 1) == (int)gridDim.x - 1) {
-            if (k > 0) r.sc->counts[r.x] = n2;
-            r.sc->fill_cursor = 0;
-            r.sc->fill_done = 0;
-        }
-    }
-}
-
-void launch_fill_multi(const ReconcileArgs& r, int blocks, cudaStream_t st)
-{
-    k_fill_multi<<<blocks, 256, 0, st>>>(r);
-}
-
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
 {
     k_reconcile<<<blocks, threads, 0, st>>>(r);

@@ -1068,6 +1068,112 @@ void graph_cache_clear(psc_lattice* L)
         if (G.exec) cudaGraphExecDestroy(G.exec);
     L->graphs.clear();
     L->graph_seen.clear();
+    for (auto& G : L->graphs1)
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+    L->graphs1.clear();
+    L->graph_seen1.clear();
+}
+
+// One event of species s (time t) replayed from a CUDA graph: its launches are
+// fixed by the species, the event's parity, the claim tables' fill and whether
+// the species' list is re-sorted after it; the event index comes from device
+// memory.  Met for the first time, the event runs as usual; met again, it is
+// captured once and replayed from then on.  For workloads whose runs of many
+// events never recur (species with unrelated hop intervals), where launching
+// dominates.  A failed capture turns graphs off for the lattice.
+static int single_event(psc_lattice* L, int s, double t)
+{
+    auto finish = [&]() {
+        L->sp[s].done++;
+        L->g++;
+        L->clock = t;
+    };
+    if (L->opt.graph_events < 2 || L->opt.time_kernels > 0 || L->g == UINT32_MAX - 1) {
+        int rc = enqueue_event(L, s);
+        finish();
+        return rc;
+    }
+    const uint8_t resort_now =
+        (L->opt.resort_period > 0 && L->since_resort[s] + 1 >= (uint64_t)L->opt.resort_period) ? 1 : 0;
+    std::vector<uint8_t> key;
+    key.push_back((uint8_t)s);
+    key.push_back((uint8_t)(L->g & 1u));
+    key.push_back(resort_now);
+    const uint8_t* tu = reinterpret_cast<const uint8_t*>(L->table_used);
+    key.insert(key.end(), tu, tu + sizeof(L->table_used));
+    for (const auto& G : L->graphs1) {
+        if (G.key != key) continue;
+        launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+        int rc = cuda_fail(L, cudaGraphLaunch(G.exec, L->stream));
+        if (rc) return rc;
+        L->table_used[0] = G.table_used[0];
+        L->table_used[1] = G.table_used[1];
+        L->since_resort[s] = resort_now ? 0 : L->since_resort[s] + 1;
+        L->launches += G.launches + 1;
+        L->events += 1;
+        finish();
+        return PSC_OK;
+    }
+    if (std::find(L->graph_seen1.begin(), L->graph_seen1.end(), key) == L->graph_seen1.end()) {
+        if (L->graph_seen1.size() >= 256) L->graph_seen1.erase(L->graph_seen1.begin());
+        L->graph_seen1.push_back(key);
+        int rc = enqueue_event(L, s);
+        finish();
+        return rc;
+    }
+    // seen before: capture once, then launch the graph
+    const uint64_t since0 = L->since_resort[s];
+    const uint32_t used0[2] = {L->table_used[0], L->table_used[1]};
+    const int64_t launches0 = L->launches;
+    const uint64_t events0 = L->events;
+    const int sticky0 = L->sticky;
+    auto restore = [&]() {
+        L->since_resort[s] = since0;
+        L->table_used[0] = used0[0];
+        L->table_used[1] = used0[1];
+        L->launches = launches0;
+        L->events = events0;
+        L->sticky = sticky0;
+        L->opt.graph_events = 0;
+        cudaGetLastError();
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        L->capture_g0 = L->g;
+        int rc = enqueue_event(L, s);
+        L->capture_g0 = -1;
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(L->stream, &graph);
+        if (rc == PSC_OK && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != PSC_OK || ce != cudaSuccess) {
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (!exec) {                                   // no graphs for this lattice: the ordinary way
+        restore();
+        int rc = enqueue_event(L, s);
+        finish();
+        return rc;
+    }
+    psc_lattice::GraphRun G;
+    G.key = key;
+    G.exec = exec;
+    G.table_used[0] = L->table_used[0];
+    G.table_used[1] = L->table_used[1];
+    G.launches = L->launches - launches0;
+    if (L->graphs1.size() >= 128) {
+        cudaGraphExecDestroy(L->graphs1.front().exec);
+        L->graphs1.erase(L->graphs1.begin());
+    }
+    L->graphs1.push_back(std::move(G));
+    launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+    int rc = cuda_fail(L, cudaGraphLaunch(exec, L->stream));
+    if (rc) return rc;
+    L->launches += 1;
+    finish();
+    return PSC_OK;
 }
 
 // Runs of per-event launches replayed from CUDA graphs (psc_options.
@@ -1141,10 +1247,9 @@ static int graph_run(psc_lattice* L, double t_end, int64_t room, int64_t* done)
     if (std::find(L->graph_seen.begin(), L->graph_seen.end(), key) == L->graph_seen.end()) {
         if (L->graph_seen.size() >= 32) L->graph_seen.erase(L->graph_seen.begin());
         L->graph_seen.push_back(key);
-        for (int e = 0; e < K; ++e) {
-            int rc = enqueue_event(L, seq[(size_t)e]);
+        for (int e = 0; e < K; ++e) {                // event by event, each from its own graph
+            int rc = single_event(L, seq[(size_t)e], at[(size_t)e]);
             if (rc) return rc;
-            advance(e);
         }
         *done = K;
         return PSC_OK;
@@ -1297,11 +1402,8 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
                 continue;
             }
         }
-        int rc = enqueue_event(L, s);
+        int rc = single_event(L, s, t);
         if (rc) return rc;
-        L->sp[s].done++;
-        L->g++;
-        L->clock = t;
         ++queued;
     }
     return PSC_OK;

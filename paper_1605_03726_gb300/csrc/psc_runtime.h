@@ -115,6 +115,9 @@ struct psc_lattice {
     };
     std::vector<GraphRun> graphs;
     std::vector<std::vector<uint8_t>> graph_seen;
+    // single events replayed from graphs (runs whose pattern does not recur)
+    std::vector<GraphRun> graphs1;
+    std::vector<std::vector<uint8_t>> graph_seen1;
     int64_t capture_g0 = -1;
 
     // tile kernel buffers (allocated on first use, grown when a plan needs more)

@@ -408,19 +408,23 @@ int  psc_batch_run(psc_batch *B, double t_end);
 int64_t psc_batch_launches(const psc_batch *B);
 void psc_batch_destroy(psc_batch *B);
 
-/* Batch autotuner: threads per block (128, 256) and the most blocks one
-   member's event gets in a batched launch (8 .. 256, the rest grid-strided),
+/* Batch autotuner: threads per block (128, 256), the most blocks one
+   member's event gets in a batched launch (8 .. 256, the rest grid-strided:
+   with the threads, the molecules each thread takes), then the members'
+   Morton re-sort period (never, or every 64 or 256 of a member's events),
    chosen by timing windows of batched events (CUDA events on the batch's
    stream).  Trial rounds are real events of every member (results are the
-   same under any block shape); at most max_rounds batched events run.  The
-   chosen shape stays set for the batch.  Errors: PSC_E_ARG, PSC_E_CUDA. */
+   same under any block shape and list order); at most max_rounds batched
+   events run.  The chosen options stay set for the batch.  Errors:
+   PSC_E_ARG, PSC_E_CUDA. */
 typedef struct {
     int32_t threads;
     int32_t blocks_per_member;
     int32_t trials;
     int64_t rounds;            /* batched events the trials ran              */
-    double  us_per_round;      /* of the chosen shape                        */
+    double  us_per_round;      /* of the chosen options                      */
     double  us_per_round_before;
+    int32_t resort_period;     /* chosen re-sort period of the members (-1 never) */
 } psc_batch_tune_result;
 int psc_batch_autotune(psc_batch *B, int64_t max_rounds, psc_batch_tune_result *out);
 

@@ -76,7 +76,7 @@ class TuneResult(ctypes.Structure):
 class BatchTuneResult(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("blocks_per_member", ctypes.c_int32), ("trials", ctypes.c_int32),
                 ("rounds", ctypes.c_int64), ("us_per_round", ctypes.c_double),
-                ("us_per_round_before", ctypes.c_double)]
+                ("us_per_round_before", ctypes.c_double), ("resort_period", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if t is ctypes.c_double else int(getattr(self, n)))

@@ -41,6 +41,7 @@ struct psc_batch {
     int64_t launches = 0;
     int threads = kItemThreadsDefault;
     int item_blocks_max = kItemBlocksMaxDefault;
+    int32_t resort_period = -1;           // events of a member's species between Morton re-sorts (-1 never)
 };
 
 namespace {
@@ -133,6 +134,16 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
         L->clock = acts[a].t;
         L->events++;
         L->launches += 2;
+        // the member's list in Morton order again every resort_period of its events (the order of a
+        // list never changes results)
+        if (B->resort_period > 0 && ++L->since_resort[acts[a].s] >= (uint64_t)B->resort_period) {
+            L->since_resort[acts[a].s] = 0;
+            const int rc = psc_rt::resort(L, acts[a].s);
+            if (rc) {
+                *rc_out = rc;
+                return na;
+            }
+        }
     }
     return na;
 }
@@ -315,10 +326,23 @@ int psc_batch_autotune(psc_batch* B, int64_t max_rounds, psc_batch_tune_result* 
     }
     B->threads = best_t;
     B->item_blocks_max = best_m;
+    // the members' re-sort period: none, or every 64 or 256 of a member's
+    // events; each trial spans at least one period of the fastest member
+    int best_r = B->resort_period;
+    for (const int period : {-1, 64, 256}) {
+        if (rc || budget <= 0) break;
+        if (period == best_r) continue;
+        B->resort_period = period;
+        double us;
+        const int64_t span = period > 0 ? std::max<int64_t>(W, period) : W;
+        if (!(rc = rounds(span, true, &us)) && us < best_us) { best_us = us; best_r = period; }
+    }
+    B->resort_period = best_r;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     out->threads = best_t;
     out->blocks_per_member = best_m;
+    out->resort_period = best_r;
     out->us_per_round = best_us;
     return rc;
 }

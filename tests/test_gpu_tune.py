@@ -115,3 +115,33 @@ def test_tuned_small_reaction_lattice_with_graph_trials():
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     print("tuned:", r)
     g.close()
+
+
+def test_batch_tuner_tries_resort_periods_and_results_stay():
+    # with room for every trial, the batch tuner also times the members'
+    # Morton re-sort period (never, 64, 256 events); list order never changes
+    # results, so members still equal their solo runs
+    import torch
+    stream = torch.cuda.Stream()
+    B = psc.Batch(stream=stream.cuda_stream)
+    members, solos = [], []
+    for r, e in enumerate((24, 32, 40, 28)):
+        n = int(0.04 * e ** 3)
+        for dst, st in ((members, stream.cuda_stream), (solos, None)):
+            L = psc.Lattice(e, e, e, voxel_radius=1e-8, stream=st)
+            L.set_options(claim_table=1, resort_period=-1)
+            models.reaction_diffusion_ab(L, n, n)
+            L.populate(700 + r)
+            dst.append(L)
+        B.add(members[-1])
+    res = B.autotune(900)
+    assert res["resort_period"] in (-1, 64, 256)
+    assert res["trials"] >= 14 and res["rounds"] <= 900
+    B.run_events(70)
+    for m, s in zip(members, solos):
+        s.run_events(m.event_index())
+        assert np.array_equal(m.grid(), s.grid())
+        for sp in range(3):
+            a, b = m.coords(sp), s.coords(sp)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    B.close()

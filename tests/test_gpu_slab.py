@@ -126,3 +126,25 @@ def test_slab_refusals():
             psc.Slab(L, w, 0, count)
         assert e.value.rc == psc.E_DIMS
     L.close()
+
+
+@pytest.mark.slow
+def test_slabs_at_full_size_match_the_whole_lattice():
+    # the 512^3 lattice at 1 % occupancy split into four slabs of 128 layers:
+    # after 30 events every molecule stands where the whole lattice's run put
+    # it (the whole lattice's stretch kernels are themselves checked against
+    # the oracle at this size, test_gpu_parity.py)
+    n = int(0.01 * 512 ** 3)
+    L = psc.Lattice(512, 512, 512, voxel_radius=1e-8)
+    s = L.add_species(10e-12, n)
+    L.populate(3)
+    slabs = [psc.Slab(L, s, q, 4) for q in range(4)]
+    psc.run_slabs(slabs, 30)
+    L.run_events(30)
+    ijk, ids, xyz = _gather(slabs)
+    li, lid = L.coords(s)
+    lu, _ = L.unwrapped(s)
+    assert np.array_equal(ids, lid) and np.array_equal(ijk, li) and np.array_equal(xyz, lu)
+    for sl in slabs:
+        sl.close()
+    L.close()

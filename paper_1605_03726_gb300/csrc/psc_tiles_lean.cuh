@@ -26,7 +26,11 @@
 //   - the commit phase handles every molecule in one pass: hops inside the
 //     box update the box (and, for the outermost brick layer, the global
 //     mirror), global claim words are read back in batches of loads, and
-//     departures go to the outbox, with no deferred queue.
+//     departures go to the outbox (one inbox atomic per destination box and
+//     warp when it is flushed), with no deferred queue;
+//   - whether a word is in the region's outermost brick layer comes from a
+//     bitmap in shared memory; the next chunk's bucket entries load while one
+//     is processed.
 
 constexpr uint32_t kLeanOff = 4u | (4u << 11) | (2u << 22);   // region -> box coordinates
 
@@ -395,7 +399,7 @@ __device__ __forceinline__ void lean_ingest(const TileArgs& A, int r, const Tile
 __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(const TileArgs A)
 {
     extern __shared__ uint32_t smem[];
-    // s_misc: arrivals, survivors, outbox entries, wait flag, -, commit queue
+    // s_misc: -, survivors, outbox entries, wait flag (1 until a wait times out), -, -
     __shared__ int s_misc[6];
     const EventArgs& a = A.ev;
     const Geometry& G = a.geo;
@@ -513,7 +517,6 @@ __global__ void __launch_bounds__(kTileThreads, kTileBlocksPerSM) k_tile_lean(co
         if (threadIdx.x == 0) {
             s_misc[1] = 0;
             s_misc[2] = 0;
-            s_misc[5] = 0;
         }
         // a claim word is touched only by boxes that are all neighbours of each other
         if (!lean_phase_sync(A, A.claimed, r, (uint32_t)(e + 1), &s_misc[3])) return;

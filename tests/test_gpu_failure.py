@@ -65,10 +65,18 @@ def test_barrier_wait_runs_out_and_is_reported():
     G.close()
 
 
-def test_tile_neighbour_wait_runs_out_and_is_reported():
-    # the tile kernel's phases wait on neighbouring boxes' flags, bounded the same way
+@pytest.mark.parametrize("regions,lean", [(8, 0), (16, 1)])
+def test_tile_neighbour_wait_runs_out_and_is_reported(regions, lean):
+    # the tile kernels' phases wait on neighbouring boxes' flags, bounded the
+    # same way; 8 boxes (one along i) take the general kernel, 16 the lean one
+    G0 = psc.Lattice(*SHAPE, voxel_radius=1e-8)
+    G0.set_options(persistent=1, tiles=1, tile_regions=regions, time_kernels=1)
+    _walkers(G0)
+    G0.run_events(2)
+    assert (G0.kernel_times()["tile_lean_events"] > 0) == bool(lean)
+    G0.close()
     L = psc.Lattice(*SHAPE, voxel_radius=1e-8)
-    L.set_options(persistent=1, tiles=1, tile_regions=8, barrier_timeout_us=20000, barrier_phantom=1)
+    L.set_options(persistent=1, tiles=1, tile_regions=regions, barrier_timeout_us=20000, barrier_phantom=1)
     _walkers(L)
     t0 = time.monotonic()
     L.run_events(4)
@@ -78,7 +86,7 @@ def test_tile_neighbour_wait_runs_out_and_is_reported():
     assert time.monotonic() - t0 < 10.0
     L.close()
     G = psc.Lattice(*SHAPE, voxel_radius=1e-8)
-    G.set_options(persistent=1, tiles=1, tile_regions=8)
+    G.set_options(persistent=1, tiles=1, tile_regions=regions)
     s = _walkers(G)
     G.run_events(8)
     o = oracle.Lattice(*SHAPE, 1e-8, oracle.PERIODIC_ALL, oracle.RULE_SYNC)

@@ -46,6 +46,8 @@ SLAB_CASES = [
     ((40, 32, 32), psc.PERIODIC_J | psc.PERIODIC_K, 4, 0.1, 0.15),
     ((36, 30, 20), psc.PERIODIC_I, 5, 0.0, 0.60),
     ((32, 32, 16), psc.PERIODIC_ALL, 1, 0.0, 0.10),
+    ((32, 28, 12), 0, 1, 0.05, 0.20),
+    ((40, 36, 24), psc.PERIODIC_I | psc.PERIODIC_J, 6, 0.0, 0.35),
 ]
 
 
@@ -125,6 +127,13 @@ def test_slab_refusals():
         with pytest.raises(psc.EngineError) as e:
             psc.Slab(L, w, 0, count)
         assert e.value.rc == psc.E_DIMS
+    L.close()
+    L = psc.Lattice(32, 32, 18, voxel_radius=1e-8, boundary=psc.PERIODIC_ALL | psc.FCC)
+    w = L.add_species(1e-12, 500)
+    L.populate(1)
+    with pytest.raises(psc.EngineError) as e:
+        psc.Slab(L, w, 0, 2)                  # HCP only
+    assert e.value.rc == psc.E_UNSUPPORTED
     L.close()
 
 

@@ -130,9 +130,11 @@ EventArgs event_args(const psc_lattice* L, int s)
     a.dirty[0] = L->dirty[0];
     a.dirty[1] = L->dirty[1];
     a.dirty_words = L->dirty_words;
-    // the claim outcomes live in the scratch list between claim and commit
-    // (its capacity is the largest list's; the list passes that use it come after)
-    a.dec = reinterpret_cast<uint8_t*>(L->tmp.vox);
+    // the claim outcomes live in the scratch list's third array between claim
+    // and commit, the due species' leavers in its first (its capacity is the
+    // largest list's; the list passes that use it come after)
+    a.dec = reinterpret_cast<uint8_t*>(L->tmp.img);
+    a.leave = L->tmp.vox;
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;
@@ -226,11 +228,16 @@ int enqueue_event(psc_lattice* L, int s)
     }
     sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
     for (int x : L->reconcile[s]) {
+        // the due species' own list changes only through its own molecules,
+        // whose commit already noted the leavers: fill only; a partner's list
+        // is checked against the grid first
         const ReconcileArgs r = reconcile_args(L, x);
-        const int rb = event_blocks(L, L->cap[x]);
-        launch_reconcile(r, rb, threads, L->stream);
+        if (x != s) {
+            launch_reconcile(r, event_blocks(L, L->cap[x]), threads, L->stream);
+            L->launches += 1;
+        }
         launch_fill(r, L->stream);
-        L->launches += 2;
+        L->launches += 1;
     }
     if (L->fo2[s]) {
         launch_births(a, L->stream);

@@ -102,9 +102,13 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
         }
         if (bl.n == 0) break;
         bl.total_blocks = total;
-        launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
+        // list 0 is the due species' own, whose leavers its commit noted: fill only
+        if (k > 0) {
+            launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
+            B->launches += 1;
+        }
         launch_fill_batch(B->tmpl_rc, bl, B->stream);
-        B->launches += 2;
+        B->launches += 1;
     }
     bl.n = 0;
     for (int a = 0; a < na; ++a) {

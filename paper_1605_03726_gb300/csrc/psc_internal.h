@@ -151,6 +151,8 @@ struct EventArgs {
     uint32_t* dirty[2];        // by event parity: a bit per mirror word whose voxels changed species
     uint32_t dirty_words;      // words of one dirty map
     uint8_t* dec;              // null, or per list entry the claim's outcome for the commit (kDec*)
+    int32_t* leave;            // species with reactions: the commit notes here the slots of the due
+                               // species' entries that react away (count in Scalars::tmp_count[s])
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;

@@ -464,6 +464,32 @@ __global__ void __launch_bounds__(256) k_claim(const EventArgs a)
 // ---------------------------------------------------------------------------
 // commit
 // ---------------------------------------------------------------------------
+// The mover at list slot idx (voxel v) now stands as species code nc on its
+// voxel (0: gone).  Unless it is still the due species, its entry leaves the
+// list (slot noted for the fill pass, voxel marked -1) and, for a product,
+// joins the product's list with its id and wrap counters.  Only a molecule's
+// own action changes an entry of the due species' list, so this replaces the
+// list's check against the grid.
+__device__ __forceinline__ void mover_leaves(const EventArgs& a, int idx, uint32_t v, uint32_t id, uint16_t nc)
+{
+    if (nc == (uint16_t)(a.s + 1)) return;
+    const int slot = atomicAdd(&a.sc->tmp_count[a.s], 1);
+    a.leave[slot] = idx;
+    const uint64_t img = a.list.img[idx];
+    a.list.vox[idx] = -1;
+    if (nc == 0 || nc == kBlocked) return;
+    const int y = (int)nc - 1;
+    const SpeciesList dst = a.model->lists[y];
+    const int s2 = atomicAdd(&a.sc->counts[y], 1);
+    if (s2 < dst.cap) {
+        dst.vox[s2] = (int32_t)v;
+        dst.ids[s2] = id;
+        dst.img[s2] = img;
+    } else {
+        atomicOr(&a.sc->err, kErrListOverflow);
+    }
+}
+
 template <bool GENERAL, bool HASH>
 __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int blk, int nblk)
 {
@@ -515,6 +541,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                         a.occ[nb.t] = (uint16_t)(R.p1 + 1);
                         bit_set(pb, bt);
                         mark_dirty(dirty, bv.word);
+                        mover_leaves(a, idx, v, id, (uint16_t)(R.p0 + 1));
                         const int slot = atomicAdd(&a.sc->births, 1);
                         if (slot < a.births_cap) {
                             Birth b;
@@ -535,6 +562,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
                         bit_clear(a.bits, bv);
                     }
                     mark_dirty(dirty, bv.word);
+                    mover_leaves(a, idx, v, id, R.np ? (uint16_t)(R.p0 + 1) : (uint16_t)0);
                     ++n_r1;
                 }
                 continue;
@@ -587,6 +615,7 @@ __device__ __forceinline__ void commit_body(const EventArgs& a, uint32_t g, int 
             }
             mark_dirty(dirty, bt.word);
             mark_dirty(dirty, bv.word);
+            mover_leaves(a, idx, v, id, a.occ[v]);
             ++n_r2;
         }
     }

@@ -96,6 +96,61 @@ int event_blocks(const psc_lattice* L, int64_t work)
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
+// Grid of a per-event launch over list x: the list's grid class (4, 32 or
+// 256 blocks, or the full grid for its capacity).
+int list_blocks(const psc_lattice* L, int x)
+{
+    return std::min(event_blocks(L, L->cap[x]), L->grid_class[x]);
+}
+
+// The grid class for a list estimated at n entries, given its class so far:
+// a class holds at least one block per 128 entries; it grows as soon as the
+// list outgrows it and shrinks only once the list needs a sixteenth of it, so
+// that captured graphs (keyed by the grids) stay valid while a count hovers.
+static int grid_class_for(const psc_lattice* L, int x, int64_t n, int cur)
+{
+    static const int kClasses[3] = {4, 32, 256};
+    const int full = event_blocks(L, L->cap[x]);
+    const int64_t need = (2 * n + L->opt.block_threads - 1) / L->opt.block_threads + 1;
+    int fit = INT32_MAX;
+    for (int c : kClasses)
+        if (need <= c && c < full) { fit = c; break; }
+    if (cur <= 0 || fit > cur) return fit;                      // first class, or grown out of it
+    const int64_t cur_blocks = std::min(cur, full);
+    return need * 16 <= cur_blocks ? fit : cur;
+}
+
+// Take the last background copy of the list lengths if it has landed, and
+// start the next one every 64 events.  The host queues events far faster than
+// the device runs them; once a copy is 256 events old the host waits for it,
+// so the estimates stay recent (the device still has that many queued).
+void refresh_estimates(psc_lattice* L)
+{
+    if (!L->counts_h) return;
+    if (L->counts_pending) {
+        if (cudaEventQuery(L->counts_ev) != cudaSuccess) {
+            if (L->g - L->counts_g < 256u) return;
+            if (cudaEventSynchronize(L->counts_ev) != cudaSuccess) {
+                L->counts_pending = false;
+                return;
+            }
+        }
+        for (int s = 0; s < L->nsp; ++s) {
+            L->est[s] = L->counts_h[s];
+            L->grid_class[s] = grid_class_for(L, s, L->est[s], L->grid_class[s]);
+        }
+        L->counts_pending = false;
+    }
+    if (L->g - L->counts_g < 64u) return;
+    if (cudaMemcpyAsync(L->counts_h, L->sc->counts, sizeof(int32_t) * (size_t)L->nsp, cudaMemcpyDeviceToHost,
+                        L->stream) != cudaSuccess ||
+        cudaEventRecord(L->counts_ev, L->stream) != cudaSuccess)
+        return;
+    L->d2h += sizeof(int32_t) * (size_t)L->nsp;
+    L->counts_pending = true;
+    L->counts_g = L->g;
+}
+
 // set-up of one event of species s, everything passed by value
 EventArgs event_args(const psc_lattice* L, int s)
 {
@@ -135,6 +190,7 @@ EventArgs event_args(const psc_lattice* L, int s)
     // largest list's; the list passes that use it come after)
     a.dec = reinterpret_cast<uint8_t*>(L->tmp.img);
     a.leave = L->tmp.vox;
+    a.g_bump = nullptr;
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
     return a;
@@ -174,7 +230,7 @@ void span_close(psc_lattice* L, cudaEvent_t a, int kind, int64_t events = 1)
 
 int resort(psc_lattice* L, int s)
 {
-    const int blocks = event_blocks(L, L->cap[s]);
+    const int blocks = list_blocks(L, s);
     const SpeciesList& list = L->model_h.lists[s];
     const int32_t* count = &L->sc->counts[s];
     launch_morton_keys(list, count, L->geo, L->rs_keys, L->rs_vals, blocks, L->stream);
@@ -202,6 +258,7 @@ ReconcileArgs reconcile_args(const psc_lattice* L, int x)
     r.dirty[1] = L->dirty[1];
     r.g = L->g;
     r.g_base = nullptr;
+    r.g_bump = nullptr;
     if (L->capture_g0 >= 0) {
         r.g = L->g - (uint32_t)L->capture_g0;
         r.g_base = &L->sc->g_base;
@@ -213,7 +270,7 @@ int enqueue_event(psc_lattice* L, int s)
 {
     const EventArgs a = event_args(L, s);
     const int threads = L->opt.block_threads;
-    const int blocks = event_blocks(L, L->cap[s]);
+    const int blocks = list_blocks(L, s);
     cudaEvent_t sp = span_open(L);
     launch_claim(a, L->general[s], blocks, threads, L->stream);
     span_close(L, sp, kSpanClaim);
@@ -227,20 +284,27 @@ int enqueue_event(psc_lattice* L, int s)
         L->table_used[cur ^ 1] = 0;
     }
     sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
-    for (int x : L->reconcile[s]) {
+    // captured as a single-event graph: the event's last launch advances the
+    // device's event index to the next event
+    uint32_t* bump = L->capture_single ? &L->sc->g_base : nullptr;
+    for (size_t q = 0; q < L->reconcile[s].size(); ++q) {
         // the due species' own list changes only through its own molecules,
         // whose commit already noted the leavers: fill only; a partner's list
         // is checked against the grid first
-        const ReconcileArgs r = reconcile_args(L, x);
+        const int x = L->reconcile[s][q];
+        ReconcileArgs r = reconcile_args(L, x);
         if (x != s) {
-            launch_reconcile(r, event_blocks(L, L->cap[x]), threads, L->stream);
+            launch_reconcile(r, list_blocks(L, x), threads, L->stream);
             L->launches += 1;
         }
+        if (!L->fo2[s] && q + 1 == L->reconcile[s].size()) r.g_bump = bump;
         launch_fill(r, L->stream);
         L->launches += 1;
     }
     if (L->fo2[s]) {
-        launch_births(a, L->stream);
+        EventArgs ab = a;
+        ab.g_bump = bump;
+        launch_births(ab, L->stream);
         L->launches += 1;
     }
     span_close(L, sp, kSpanReconcile);
@@ -1062,12 +1126,44 @@ int psc_populate(psc_lattice* L, uint64_t seed)
     L->g = 0;
     L->clock = 0.0;
     L->populated = true;
+    // the list-length estimates start from the placed counts (without the
+    // pinned copy the grids follow the capacities)
+    for (int s = 0; s < L->nsp; ++s) {
+        L->est[s] = L->sp[s].n0;
+        L->grid_class[s] = INT32_MAX;
+    }
+    L->counts_g = 0;
+    if (!L->counts_h && cudaMallocHost(&L->counts_h, sizeof(int32_t) * kMaxSpecies) != cudaSuccess) {
+        L->counts_h = nullptr;
+        cudaGetLastError();
+    }
+    if (L->counts_h && !L->counts_ev &&
+        cudaEventCreateWithFlags(&L->counts_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(L->counts_h);
+        L->counts_h = nullptr;
+        L->counts_ev = nullptr;
+        cudaGetLastError();
+    }
+    // lists that start empty take the full grid until their first estimate
+    if (L->counts_h)
+        for (int s = 0; s < L->nsp; ++s)
+            if (L->est[s] > 0) L->grid_class[s] = grid_class_for(L, s, L->est[s], 0);
     return L->clamped ? PSC_W_PCLAMP : PSC_OK;
 }
 
 }  // extern "C"
 
 namespace psc_rt {
+
+// The per-event grids a captured event takes (they follow the list estimates).
+static void append_grids(const psc_lattice* L, std::vector<uint8_t>& key)
+{
+    for (int x = 0; x < L->nsp; ++x) {
+        const int b = list_blocks(L, x);
+        key.push_back((uint8_t)(b & 0xFF));
+        key.push_back((uint8_t)(b >> 8));
+    }
+}
 
 void graph_cache_clear(psc_lattice* L)
 {
@@ -1108,15 +1204,25 @@ static int single_event(psc_lattice* L, int s, double t)
     key.push_back(resort_now);
     const uint8_t* tu = reinterpret_cast<const uint8_t*>(L->table_used);
     key.insert(key.end(), tu, tu + sizeof(L->table_used));
+    append_grids(L, key);
+    // the event index: events of species with reactions advance it on the
+    // device, so a run of their replays sets it once
+    auto set_index = [&]() {
+        if (L->g_dev != (int64_t)L->g) {
+            launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+            L->launches += 1;
+        }
+        L->g_dev = L->general[s] ? (int64_t)L->g + 1 : (int64_t)L->g;
+    };
     for (const auto& G : L->graphs1) {
         if (G.key != key) continue;
-        launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+        set_index();
         int rc = cuda_fail(L, cudaGraphLaunch(G.exec, L->stream));
         if (rc) return rc;
         L->table_used[0] = G.table_used[0];
         L->table_used[1] = G.table_used[1];
         L->since_resort[s] = resort_now ? 0 : L->since_resort[s] + 1;
-        L->launches += G.launches + 1;
+        L->launches += G.launches;
         L->events += 1;
         finish();
         return PSC_OK;
@@ -1147,8 +1253,10 @@ static int single_event(psc_lattice* L, int s, double t)
     cudaGraphExec_t exec = nullptr;
     if (cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         L->capture_g0 = L->g;
+        L->capture_single = true;
         int rc = enqueue_event(L, s);
         L->capture_g0 = -1;
+        L->capture_single = false;
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamEndCapture(L->stream, &graph);
         if (rc == PSC_OK && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -1175,10 +1283,9 @@ static int single_event(psc_lattice* L, int s, double t)
         L->graphs1.erase(L->graphs1.begin());
     }
     L->graphs1.push_back(std::move(G));
-    launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+    set_index();
     int rc = cuda_fail(L, cudaGraphLaunch(exec, L->stream));
     if (rc) return rc;
-    L->launches += 1;
     finish();
     return PSC_OK;
 }
@@ -1231,6 +1338,7 @@ static int graph_run(psc_lattice* L, double t_end, int64_t room, int64_t* done)
     put(L->table_used, sizeof(L->table_used));
     for (int s = 0; s < L->nsp; ++s)                 // only the run's species can re-sort in it
         if (in_run[s]) put(&L->since_resort[s], sizeof(uint64_t));
+    append_grids(L, key);
     auto advance = [&](int e) {
         L->sp[seq[(size_t)e]].done++;
         L->g++;
@@ -1239,6 +1347,7 @@ static int graph_run(psc_lattice* L, double t_end, int64_t room, int64_t* done)
     for (const auto& G : L->graphs) {
         if (G.key != key) continue;
         launch_fill_u32(&L->sc->g_base, L->g, 1, 1, L->stream);
+        L->g_dev = (int64_t)L->g;
         int rc = cuda_fail(L, cudaGraphLaunch(G.exec, L->stream));
         if (rc) return rc;
         for (int e = 0; e < K; ++e) advance(e);
@@ -1315,6 +1424,7 @@ static int graph_run(psc_lattice* L, double t_end, int64_t room, int64_t* done)
     }
     L->graphs.push_back(std::move(G));
     launch_fill_u32(&L->sc->g_base, g0, 1, 1, L->stream);
+    L->g_dev = (int64_t)g0;
     if ((rc = cuda_fail(L, cudaGraphLaunch(exec, L->stream)))) return rc;
     L->launches += 1;
     *done = K;
@@ -1331,6 +1441,7 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
         int s;
         double t;
         if (!next_event(L, &s, &t) || t > t_end) break;
+        refresh_estimates(L);
         if (L->g == UINT32_MAX) return PSC_E_LIMIT;
         if (L->opt.subvolume > 0) {
             // the sub-volume rule: stretches of the species' events, one launch each
@@ -1764,6 +1875,8 @@ void psc_lattice_destroy(psc_lattice* L)
         if (L->stream) cudaStreamSynchronize(L->stream);
         for (const auto& sp : L->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
         for (cudaEvent_t ev : L->event_pool) cudaEventDestroy(ev);
+        if (L->counts_ev) cudaEventDestroy(L->counts_ev);
+        if (L->counts_h) cudaFreeHost(L->counts_h);
         graph_cache_clear(L);
         dev_free_all(L);
         if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);

@@ -153,6 +153,7 @@ struct EventArgs {
     uint8_t* dec;              // null, or per list entry the claim's outcome for the commit (kDec*)
     int32_t* leave;            // species with reactions: the commit notes here the slots of the due
                                // species' entries that react away (count in Scalars::tmp_count[s])
+    uint32_t* g_bump;          // null, or the word the event's last launch sets to its index + 1
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;
@@ -250,6 +251,7 @@ struct ReconcileArgs {
     const uint32_t* dirty[2];  // the commit's dirty maps, by event parity
     uint32_t g;                // event index (with g_base: its offset from *g_base)
     const uint32_t* g_base;
+    uint32_t* g_bump;          // null, or the word the event's last launch sets to its index + 1
 };
 
 // ---- launchers (psc_kernels.cu) ----

@@ -1066,6 +1066,7 @@ __device__ __forceinline__ void fill_body(const ReconcileArgs& r)
 __global__ void __launch_bounds__(1024) k_fill(const ReconcileArgs r)
 {
     fill_body(r);
+    if (threadIdx.x == 0 && r.g_bump) *r.g_bump = reconcile_event(r) + 1u;
 }
 
 void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
@@ -1135,6 +1136,7 @@ __device__ __forceinline__ void births_body(const EventArgs& a)
 __global__ void __launch_bounds__(1024) k_births(const EventArgs a)
 {
     births_body(a);
+    if (threadIdx.x == 0 && a.g_bump) *a.g_bump = event_index(a) + 1u;
 }
 
 void launch_births(const EventArgs& a, cudaStream_t st)

@@ -119,6 +119,18 @@ struct psc_lattice {
     std::vector<GraphRun> graphs1;
     std::vector<std::vector<uint8_t>> graph_seen1;
     int64_t capture_g0 = -1;
+    bool capture_single = false;
+    // Host estimates of the list lengths, for the per-event grids only (every
+    // per-event kernel strides over the count in device memory, so a stale
+    // estimate costs time, never results): a pinned copy of Scalars::counts
+    // refreshed in the background every few events.
+    int64_t est[kMaxSpecies] = {};
+    int32_t grid_class[kMaxSpecies] = {};  // per-event grid limit of each list (INT32_MAX: none)
+    int32_t* counts_h = nullptr;
+    cudaEvent_t counts_ev = nullptr;
+    bool counts_pending = false;
+    uint32_t counts_g = 0;       // capturing one event: its last launch advances Scalars::g_base
+    int64_t g_dev = -1;                // what Scalars::g_base holds once the queued work is done (-1 unknown)
 
     // tile kernel buffers (allocated on first use, grown when a plan needs more)
     struct TileBuffers {
@@ -167,6 +179,7 @@ struct DevGuard {
 int cuda_fail(psc_lattice* L, cudaError_t e);
 void* dev_alloc(psc_lattice* L, size_t bytes);
 int event_blocks(const psc_lattice* L, int64_t work);
+int list_blocks(const psc_lattice* L, int x);
 EventArgs event_args(const psc_lattice* L, int s);
 ReconcileArgs reconcile_args(const psc_lattice* L, int x);
 bool next_event(const psc_lattice* L, int* s_out, double* t_out);

@@ -287,19 +287,36 @@ int enqueue_event(psc_lattice* L, int s)
     // captured as a single-event graph: the event's last launch advances the
     // device's event index to the next event
     uint32_t* bump = L->capture_single ? &L->sc->g_base : nullptr;
-    for (size_t q = 0; q < L->reconcile[s].size(); ++q) {
-        // the due species' own list changes only through its own molecules,
-        // whose commit already noted the leavers: fill only; a partner's list
-        // is checked against the grid first
-        const int x = L->reconcile[s][q];
-        ReconcileArgs r = reconcile_args(L, x);
+    // the due species' own list changes only through its own molecules, whose
+    // commit noted the leavers; partner lists are checked against the grid,
+    // one after the other; then one launch fills every list, a block each
+    // (list order: the due species, then the partners; each list's scratch
+    // range follows those of the lists before it)
+    const std::vector<int>& Q = L->reconcile[s];
+    uint32_t before = 0;
+    for (int x : Q) {
         if (x != s) {
-            launch_reconcile(r, list_blocks(L, x), threads, L->stream);
+            launch_reconcile(reconcile_args(L, x), before, list_blocks(L, x), threads, L->stream);
             L->launches += 1;
         }
-        if (!L->fo2[s] && q + 1 == L->reconcile[s].size()) r.g_bump = bump;
-        launch_fill(r, L->stream);
-        L->launches += 1;
+        before |= 1u << x;
+    }
+    if (!Q.empty()) {
+        ListFill f{};
+        f.r = reconcile_args(L, s);
+        before = 0;
+        for (size_t q = 0; q < Q.size(); ++q) {
+            f.x[f.n] = Q[q];
+            f.list[f.n] = L->model_h.lists[Q[q]];
+            f.before[f.n] = before;
+            before |= 1u << Q[q];
+            if (++f.n == kListFillMax || q + 1 == Q.size()) {
+                if (!L->fo2[s] && q + 1 == Q.size()) f.r.g_bump = bump;
+                launch_fill(f, L->stream);
+                L->launches += 1;
+                f.n = 0;
+            }
+        }
     }
     if (L->fo2[s]) {
         EventArgs ab = a;
@@ -975,9 +992,11 @@ int psc_populate(psc_lattice* L, uint64_t seed)
         l.img = (uint64_t*)dev_alloc(L, (size_t)l.cap * 8);
         if (!l.vox || !l.ids || !l.img) return PSC_E_NOMEM;
     }
+    // the list passes of an event note up to two leavers per reaction, at most
+    // one reaction per molecule of the due species
     L->tmp.cap = (int32_t)max_cap;
-    L->tmp.vox = (int32_t*)dev_alloc(L, (size_t)max_cap * 4);
-    L->tmp.ids = (uint32_t*)dev_alloc(L, (size_t)max_cap * 4);
+    L->tmp.vox = (int32_t*)dev_alloc(L, (size_t)max_cap * 8);
+    L->tmp.ids = (uint32_t*)dev_alloc(L, (size_t)max_cap * 8);
     L->tmp.img = (uint64_t*)dev_alloc(L, (size_t)max_cap * 8);
     if (!L->tmp.vox || !L->tmp.ids || !L->tmp.img) return PSC_E_NOMEM;
     L->births_cap = any_fo2 ? 8192 : 1;
@@ -1852,7 +1871,7 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
             mx = std::max<int64_t>(mx, L->cap[s]);
             if (L->sp[s].D > 0.0) mm = std::max<int64_t>(mm, L->cap[s]);
         }
-        b += mx * 16 + (int64_t)L->births_cap * (int64_t)sizeof(Birth) + mm * 8 +
+        b += mx * 24 + (int64_t)L->births_cap * (int64_t)sizeof(Birth) + mm * 8 +
              (int64_t)sort_scratch_bytes(mm);
     } else {
         b += 2 * N * 16 + 2 * N * 8;

@@ -78,6 +78,7 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
         it.sel = s;
         it.g = L->g;
         it.block0 = total;
+        it.mask = 0;
         total += item_blocks(B, L->cap[s]);
     }
     if (na == 0) return 0;
@@ -85,8 +86,12 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
     launch_claim_batch(B->tmpl_ev, bl, B->threads, B->stream);
     launch_commit_batch(B->tmpl_ev, bl, B->threads, B->stream);
     B->launches += 2;
-    // list passes: the k-th list each member's event touches
-    for (int k = 0;; ++k) {
+    // list passes: the k-th partner list of each member's event checked
+    // against the member's grid (list 0 is the member's own species, whose
+    // commit noted its leavers), then every list of every member's event
+    // filled, a block each; a list's scratch range follows those of the lists
+    // before it in the member's order
+    for (int k = 1;; ++k) {
         bl.n = 0;
         total = 0;
         for (int a = 0; a < na; ++a) {
@@ -98,15 +103,38 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
             it.sel = rec[k];
             it.g = L->g;                  // the event's parity picks the commit's dirty map
             it.block0 = total;
+            it.mask = 0;
+            for (int q = 0; q < k; ++q) it.mask |= 1u << rec[q];
             total += item_blocks(B, L->cap[rec[k]]);
         }
         if (bl.n == 0) break;
         bl.total_blocks = total;
-        // list 0 is the due species' own, whose leavers its commit noted: fill only
-        if (k > 0) {
-            launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
-            B->launches += 1;
+        launch_reconcile_batch(B->tmpl_rc, bl, B->threads, B->stream);
+        B->launches += 1;
+    }
+    bl.n = 0;
+    for (int a = 0; a < na; ++a) {
+        psc_lattice* L = B->slot[acts[a].slot].L;
+        const std::vector<int>& rec = L->reconcile[acts[a].s];
+        uint32_t before = 0;
+        for (int x : rec) {
+            BatchItem& it = bl.item[bl.n++];
+            it.rep = acts[a].slot;
+            it.sel = x;
+            it.g = L->g;
+            it.block0 = bl.n - 1;
+            it.mask = before;
+            before |= 1u << x;
+            if (bl.n == kBatchMax) {
+                bl.total_blocks = bl.n;
+                launch_fill_batch(B->tmpl_rc, bl, B->stream);
+                B->launches += 1;
+                bl.n = 0;
+            }
         }
+    }
+    if (bl.n > 0) {
+        bl.total_blocks = bl.n;
         launch_fill_batch(B->tmpl_rc, bl, B->stream);
         B->launches += 1;
     }
@@ -119,6 +147,7 @@ int batch_event(psc_batch* B, double t_cap, int* rc_out)
         it.sel = acts[a].s;
         it.g = L->g;
         it.block0 = bl.n;
+        it.mask = 0;
         bl.n++;
     }
     if (bl.n > 0) {

@@ -246,6 +246,7 @@ struct ReconcileArgs {
     int32_t x;                 // species whose list is reconciled
     SpeciesList list;
     SpeciesList tmp;           // scratch: the slots that leave, then the holes and the tail's survivors
+                               // (vox and ids hold twice the capacity: one reaction can remove two entries)
     const ModelDev* model;
     Scalars* sc;
     const uint32_t* dirty[2];  // the commit's dirty maps, by event parity
@@ -326,9 +327,19 @@ void launch_materialize(uint16_t* out, const uint16_t* occ, const uint32_t* bits
                         int n_mirrors, const Geometry& geo, int64_t V, int blocks, cudaStream_t st);
 void launch_scatter_codes(uint16_t* out, const SpeciesList& list, const int32_t* count, uint16_t code,
                           int blocks, cudaStream_t st);
-void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st);
-// the list's leavers' slots filled from its tail (one block)
-void launch_fill(const ReconcileArgs& r, cudaStream_t st);
+// Partner list r.x checked against the grid; its leavers' slots go after
+// those of the lists in `before` (a bit per species).
+void launch_reconcile(const ReconcileArgs& r, uint32_t before, int blocks, int threads, cudaStream_t st);
+// The event's lists filled from their tails, one block each, side by side.
+constexpr int kListFillMax = 8;
+struct ListFill {
+    ReconcileArgs r;                       // the event's arguments; x and list per block
+    int32_t n;
+    int32_t x[kListFillMax];
+    SpeciesList list[kListFillMax];
+    uint32_t before[kListFillMax];         // lists whose scratch ranges come first
+};
+void launch_fill(const ListFill& f, cudaStream_t st);
 void launch_births(const EventArgs& a, cudaStream_t st);
 void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStream_t st);
 // molecule r (ids in species order, species s owning [offsets[s],
@@ -396,6 +407,7 @@ struct BatchItem {
     int32_t sel;
     uint32_t g;
     int32_t block0;
+    uint32_t mask;             // list passes: lists whose scratch ranges come before list sel's
 };
 struct BatchLaunch {
     int32_t n;

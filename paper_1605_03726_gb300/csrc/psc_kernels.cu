@@ -973,12 +973,23 @@ __device__ __forceinline__ int warp_alloc(int* counter, bool want)
     return want ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
 }
 
-__device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, uint32_t g, int blk, int nblk)
+// The slots of the lists' leavers share the scratch arrays: list x's take the
+// range after those of the lists in `before` (the due species' own first,
+// then the partner lists in their order), so the lists fill side by side.
+__device__ __forceinline__ int32_t leave_base(const Scalars* sc, uint32_t before)
+{
+    int32_t base = 0;
+    for (uint32_t m = before; m; m &= m - 1u) base += sc->tmp_count[__ffs(m) - 1];
+    return base;
+}
+
+__device__ __forceinline__ void reconcile_body(const ReconcileArgs& r, uint32_t g, int blk, int nblk,
+                                               uint32_t before)
 {
     const int32_t n = r.sc->counts[r.x];
     const uint16_t self = (uint16_t)(r.x + 1);
     const uint32_t* dirty = r.dirty[g & 1u];
-    int32_t* leave = r.tmp.vox;                          // slots of the entries that leave
+    int32_t* leave = r.tmp.vox + leave_base(r.sc, before);   // slots of the entries that leave
     const int stride = nblk * blockDim.x;
     for (int base = blk * blockDim.x; base < n; base += stride) {
         const int idx = base + threadIdx.x;
@@ -1021,30 +1032,33 @@ __device__ __forceinline__ uint32_t reconcile_event(const ReconcileArgs& r)
     return r.g_base ? __ldcg(r.g_base) + r.g : r.g;
 }
 
-__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r)
+__global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r, uint32_t before)
 {
-    reconcile_body(r, reconcile_event(r), blockIdx.x, gridDim.x);
+    reconcile_body(r, reconcile_event(r), blockIdx.x, gridDim.x, before);
 }
 
-// One block: k entries left; the new length is n - k.  Every slot below it
-// that an entry left (a hole) takes one of the surviving entries at or above
-// it (there are as many); entries that left above it are simply cut off.
-__device__ __forceinline__ void fill_body(const ReconcileArgs& r)
+// One block per list: k entries left; the new length is n - k.  Every slot
+// below it that an entry left (a hole) takes one of the surviving entries at
+// or above it (there are as many); entries that left above it are simply cut
+// off.  The list's holes and survivors go to its range of the scratch arrays.
+__device__ __forceinline__ void fill_body(const ReconcileArgs& r, uint32_t before)
 {
     __shared__ int s_h, s_s;
     const int32_t n = r.sc->counts[r.x];
     const int32_t k = min(r.sc->tmp_count[r.x], n);
     if (k <= 0) return;
     const int32_t n2 = n - k;
-    int32_t* holes = reinterpret_cast<int32_t*>(r.tmp.ids);
-    int32_t* surv = reinterpret_cast<int32_t*>(r.tmp.img);
+    const int32_t base = leave_base(r.sc, before);
+    const int32_t* leave = r.tmp.vox + base;
+    int32_t* holes = reinterpret_cast<int32_t*>(r.tmp.ids) + base;
+    int32_t* surv = reinterpret_cast<int32_t*>(r.tmp.img) + base;
     if (threadIdx.x == 0) {
         s_h = 0;
         s_s = 0;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < k; q += blockDim.x) {
-        const int32_t h = r.tmp.vox[q];
+        const int32_t h = leave[q];
         if (h < n2) holes[atomicAdd(&s_h, 1)] = h;
     }
     for (int p = n2 + threadIdx.x; p < n; p += blockDim.x)
@@ -1063,20 +1077,25 @@ __device__ __forceinline__ void fill_body(const ReconcileArgs& r)
     }
 }
 
-__global__ void __launch_bounds__(1024) k_fill(const ReconcileArgs r)
+// block q fills list f.x[q]; block 0 advances the event index when asked
+// (no block of this launch reads it otherwise)
+__global__ void __launch_bounds__(1024) k_fill(const ListFill f)
 {
-    fill_body(r);
-    if (threadIdx.x == 0 && r.g_bump) *r.g_bump = reconcile_event(r) + 1u;
+    ReconcileArgs r = f.r;
+    r.x = f.x[blockIdx.x];
+    r.list = f.list[blockIdx.x];
+    fill_body(r, f.before[blockIdx.x]);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && r.g_bump) *r.g_bump = reconcile_event(r) + 1u;
 }
 
-void launch_reconcile(const ReconcileArgs& r, int blocks, int threads, cudaStream_t st)
+void launch_reconcile(const ReconcileArgs& r, uint32_t before, int blocks, int threads, cudaStream_t st)
 {
-    k_reconcile<<<blocks, threads, 0, st>>>(r);
+    k_reconcile<<<blocks, threads, 0, st>>>(r, before);
 }
 
-void launch_fill(const ReconcileArgs& r, cudaStream_t st)
+void launch_fill(const ListFill& f, cudaStream_t st)
 {
-    k_fill<<<1, 1024, 0, st>>>(r);
+    k_fill<<<f.n, 1024, 0, st>>>(f);
 }
 
 // ---------------------------------------------------------------------------
@@ -1490,7 +1509,7 @@ __global__ void __launch_bounds__(256) k_reconcile_batch(const ReconcileArgs* tm
     int nblk;
     const BatchItem I = bl.item[batch_find(bl, blockIdx.x, &nblk)];
     const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
-    reconcile_body(r, I.g, blockIdx.x - I.block0, nblk);
+    reconcile_body(r, I.g, blockIdx.x - I.block0, nblk, I.mask);
 }
 
 // one block per item
@@ -1498,7 +1517,7 @@ __global__ void __launch_bounds__(1024) k_fill_batch(const ReconcileArgs* tmpl, 
 {
     const BatchItem I = bl.item[blockIdx.x];
     const ReconcileArgs r = tmpl[I.rep * kMaxSpecies + I.sel];
-    fill_body(r);
+    fill_body(r, I.mask);
 }
 
 // one block per item

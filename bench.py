@@ -59,6 +59,8 @@ def parse():
                     help="replicas timed one at a time (0: all of them, the same set as the batched run)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the reaction workloads (A + B -> C 64^3, crowded 256^3, MAPK-like 200^3)")
+    ap.add_argument("--configs", default="",
+                    help="comma-separated names of the reaction workloads to run (default: all three)")
     ap.add_argument("--config-events", type=int, default=0,
                     help="events of the crowded and MAPK-like workloads (0: 650 and 4000)")
     ap.add_argument("--compartments", default="none", choices=["none", "cell"],
@@ -624,7 +626,10 @@ def reaction_arm(args, local):
     import paper_1605_03726_gb300 as psc
     hbm, peak_kind = peaks()
     out = {}
+    wanted = set(x for x in args.configs.split(",") if x)
     for w in reaction_workloads(args):
+        if wanted and w["name"] not in wanted:
+            continue
         _reaction_gpu(psc, torch, w, local, False)                # warm-up (allocations, graphs)
         run = _reaction_gpu(psc, torch, w, local, False)
         cnt = _reaction_gpu(psc, torch, w, local, True)

@@ -120,6 +120,16 @@ static int grid_class_for(const psc_lattice* L, int x, int64_t n, int cur)
     return need * 16 <= cur_blocks ? fit : cur;
 }
 
+// How many leading entries of list x a Morton re-sort takes: a list in a
+// small grid class sorts twice what its class holds, at most its capacity
+// (entries beyond keep their places; list order never changes results).  The
+// sort's tiles and scans follow this bound, not the capacity, which for
+// reaction products is the whole lattice.
+int32_t sort_limit(const psc_lattice* L, int x)
+{
+    return (int32_t)std::min<int64_t>(L->cap[x], 256 * (int64_t)L->grid_class[x]);
+}
+
 // Take the last background copy of the list lengths if it has landed, and
 // start the next one every 64 events.  The host queues events far faster than
 // the device runs them; once a copy is 256 events old the host waits for it,
@@ -233,12 +243,13 @@ int resort(psc_lattice* L, int s)
     const int blocks = list_blocks(L, s);
     const SpeciesList& list = L->model_h.lists[s];
     const int32_t* count = &L->sc->counts[s];
-    launch_morton_keys(list, count, L->geo, L->rs_keys, L->rs_vals, blocks, L->stream);
-    if (radix_sort_pairs(L->rs_keys, L->rs_vals, count, 0, L->cap[s], (int)morton_sort_bits(L->geo),
+    const int32_t limit = sort_limit(L, s);
+    launch_morton_keys(list, count, limit, L->geo, L->rs_keys, L->rs_vals, blocks, L->stream);
+    if (radix_sort_pairs(L->rs_keys, L->rs_vals, count, limit, limit, (int)morton_sort_bits(L->geo),
                          L->rs_scratch, L->stream, &L->launches) != 0)
         return cuda_fail(L, cudaErrorUnknown);
-    launch_permute(list, L->tmp, L->rs_vals, count, blocks, L->stream);
-    launch_copy_list(L->tmp, list, count, blocks, L->stream);
+    launch_permute(list, L->tmp, L->rs_vals, count, limit, blocks, L->stream);
+    launch_copy_list(L->tmp, list, count, limit, blocks, L->stream);
     L->launches += 3;
     return PSC_OK;
 }
@@ -1174,7 +1185,8 @@ int psc_populate(psc_lattice* L, uint64_t seed)
 
 namespace psc_rt {
 
-// The per-event grids a captured event takes (they follow the list estimates).
+// The per-event grids a captured event takes (they follow the list estimates;
+// so do the re-sort bounds, through the grid classes).
 static void append_grids(const psc_lattice* L, std::vector<uint8_t>& key)
 {
     for (int x = 0; x < L->nsp; ++x) {

@@ -348,12 +348,14 @@ void launch_fill_u32(uint32_t* p, uint32_t value, size_t n, int blocks, cudaStre
 void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const int64_t* offsets,
                              const int64_t* starts, int n_species, uint16_t* occ, const Geometry& geo,
                              const ModelDev* model, int blocks, cudaStream_t st);
-void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
+// The Morton re-sort of a list's first min(*count, limit) entries (the rest,
+// if any, keep their places: list order never changes results).
+void launch_morton_keys(const SpeciesList& list, const int32_t* count, int32_t limit, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st);
 uint32_t morton_sort_bits(const Geometry& geo);
 void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32_t* perm,
-                    const int32_t* count, int blocks, cudaStream_t st);
-void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count,
+                    const int32_t* count, int32_t limit, int blocks, cudaStream_t st);
+void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count, int32_t limit,
                       int blocks, cudaStream_t st);
 // set the vacancy-mirror bit of every molecule of a list (mirror cleared before)
 void launch_mirror_from_list(uint32_t* bits, const Geometry& geo, const SpeciesList& list, const int32_t* count,
@@ -422,8 +424,8 @@ void launch_births_batch(const EventArgs* tmpl, const BatchLaunch& bl, cudaStrea
 
 // ---- radix sort (psc_sort.cu) ----
 // Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
-// n is read from device memory (n_dev) or taken from n_host when n_dev is
-// null; max_n bounds it and sizes the scratch.
+// n is n_host, or the count in device memory (n_dev) capped at n_host;
+// max_n (at least n_host) sizes the tiles and the scratch.
 struct SortScratch {
     uint32_t* keys_alt = nullptr;
     uint32_t* vals_alt = nullptr;

@@ -1380,9 +1380,10 @@ void launch_populate_scatter(const uint32_t* sorted_vox, int64_t n_total, const 
 }
 
 // Morton (Z-order) key of the voxel of each list entry (compact code)
-__global__ void k_morton_keys(const SpeciesList L, const int32_t* count, Geometry G, uint32_t* keys, uint32_t* vals)
+__global__ void k_morton_keys(const SpeciesList L, const int32_t* count, int32_t limit, Geometry G, uint32_t* keys,
+                              uint32_t* vals)
 {
-    const int32_t n = *count;
+    const int32_t n = min(*count, limit);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         int32_t i, j, k;
         decode(G, (uint32_t)L.vox[idx], i, j, k);
@@ -1391,17 +1392,18 @@ __global__ void k_morton_keys(const SpeciesList L, const int32_t* count, Geometr
     }
 }
 
-void launch_morton_keys(const SpeciesList& list, const int32_t* count, const Geometry& geo,
+void launch_morton_keys(const SpeciesList& list, const int32_t* count, int32_t limit, const Geometry& geo,
                         uint32_t* keys, uint32_t* vals, int blocks, cudaStream_t st)
 {
-    k_morton_keys<<<blocks, 256, 0, st>>>(list, count, geo, keys, vals);
+    k_morton_keys<<<blocks, 256, 0, st>>>(list, count, limit, geo, keys, vals);
 }
 
 uint32_t morton_sort_bits(const Geometry& geo) { return geo.mort_bits; }
 
-__global__ void k_permute(const SpeciesList src, const SpeciesList dst, const uint32_t* perm, const int32_t* count)
+__global__ void k_permute(const SpeciesList src, const SpeciesList dst, const uint32_t* perm, const int32_t* count,
+                          int32_t limit)
 {
-    const int32_t n = *count;
+    const int32_t n = min(*count, limit);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint32_t p = perm[r];
         dst.vox[r] = src.vox[p];
@@ -1411,14 +1413,14 @@ __global__ void k_permute(const SpeciesList src, const SpeciesList dst, const ui
 }
 
 void launch_permute(const SpeciesList& src, const SpeciesList& dst, const uint32_t* perm,
-                    const int32_t* count, int blocks, cudaStream_t st)
+                    const int32_t* count, int32_t limit, int blocks, cudaStream_t st)
 {
-    k_permute<<<blocks, 256, 0, st>>>(src, dst, perm, count);
+    k_permute<<<blocks, 256, 0, st>>>(src, dst, perm, count, limit);
 }
 
-__global__ void k_copy_list(const SpeciesList src, const SpeciesList dst, const int32_t* count)
+__global__ void k_copy_list(const SpeciesList src, const SpeciesList dst, const int32_t* count, int32_t limit)
 {
-    const int32_t n = *count;
+    const int32_t n = min(*count, limit);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         dst.vox[r] = src.vox[r];
         dst.ids[r] = src.ids[r];
@@ -1426,10 +1428,10 @@ __global__ void k_copy_list(const SpeciesList src, const SpeciesList dst, const 
     }
 }
 
-void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count,
+void launch_copy_list(const SpeciesList& src, const SpeciesList& dst, const int32_t* count, int32_t limit,
                       int blocks, cudaStream_t st)
 {
-    k_copy_list<<<blocks, 256, 0, st>>>(src, dst, count);
+    k_copy_list<<<blocks, 256, 0, st>>>(src, dst, count, limit);
 }
 
 __global__ void k_mirror_from_list(uint32_t* bits, Geometry G, const SpeciesList L, const int32_t* count)

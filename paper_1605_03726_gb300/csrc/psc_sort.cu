@@ -42,9 +42,10 @@ void sort_scratch_bind(SortScratch& s, void* base, int64_t max_n)
     s.block_sums = reinterpret_cast<uint32_t*>(p);
 }
 
+// the element count: n_host, or the count in device memory capped at n_host
 __device__ __forceinline__ int64_t sort_n(const int32_t* n_dev, int64_t n_host)
 {
-    return n_dev ? (int64_t)*n_dev : n_host;
+    return n_dev ? min((int64_t)*n_dev, n_host) : n_host;
 }
 
 __global__ void __launch_bounds__(kSortThreads)

@@ -283,12 +283,20 @@ int enqueue_event(psc_lattice* L, int s)
     const int threads = L->opt.block_threads;
     const int blocks = list_blocks(L, s);
     cudaEvent_t sp = span_open(L);
-    launch_claim(a, L->general[s], blocks, threads, L->stream);
-    span_close(L, sp, kSpanClaim);
-    sp = span_open(L);
-    launch_commit(a, L->general[s], blocks, threads, L->stream);
-    span_close(L, sp, kSpanCommit);
-    L->launches += 2;
+    if (L->general[s] && L->grid_class[s] <= 4) {
+        // a list of at most a few hundred molecules: claim and commit in one
+        // block, one launch
+        launch_event_one(a, L->stream);
+        span_close(L, sp, kSpanClaim);
+        L->launches += 1;
+    } else {
+        launch_claim(a, L->general[s], blocks, threads, L->stream);
+        span_close(L, sp, kSpanClaim);
+        sp = span_open(L);
+        launch_commit(a, L->general[s], blocks, threads, L->stream);
+        span_close(L, sp, kSpanCommit);
+        L->launches += 2;
+    }
     if (L->tables[0]) {
         const int cur = (int)(L->g & 1u);
         L->table_used[cur] = 1u << L->hash_bits[s];

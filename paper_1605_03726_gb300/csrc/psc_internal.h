@@ -259,6 +259,10 @@ struct ReconcileArgs {
 void upload_stencil(cudaStream_t st);
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
 void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
+// claim and commit of one event of a species with reactions in a single block
+// (lists of a few hundred molecules)
+constexpr int kEventOneThreads = 512;
+void launch_event_one(const EventArgs& a, cudaStream_t st);
 void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st);
 // Molecules per thread the persistent kernel holds in registers (0 = the
 // stretch does not fit); threads = its launch width.

@@ -634,6 +634,26 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
     commit_body<GENERAL, HASH>(a, event_index(a), blockIdx.x, gridDim.x);
 }
 
+// A whole event of a short list of a species with reactions in one block:
+// the claim phase, a block barrier (after which every claim of the event is
+// in place and visible to the block), the commit phase.  Claims the block
+// reads back and bits it tests change only through their winner, as across
+// launches.
+template <bool HASH>
+__global__ void __launch_bounds__(kEventOneThreads) k_event_one(const EventArgs a)
+{
+    const uint32_t g = event_index(a);
+    claim_body<true, HASH>(a, g, 0, 1);
+    __syncthreads();
+    commit_body<true, HASH>(a, g, 0, 1);
+}
+
+void launch_event_one(const EventArgs& a, cudaStream_t st)
+{
+    if (a.ct.hash) k_event_one<true><<<1, kEventOneThreads, 0, st>>>(a);
+    else k_event_one<false><<<1, kEventOneThreads, 0, st>>>(a);
+}
+
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)
 {
     const bool hash = a.ct.hash != nullptr;

@@ -200,6 +200,8 @@ EventArgs event_args(const psc_lattice* L, int s)
     // largest list's; the list passes that use it come after)
     a.dec = reinterpret_cast<uint8_t*>(L->tmp.img);
     a.leave = L->tmp.vox;
+    a.holes = reinterpret_cast<int32_t*>(L->tmp.ids);
+    a.surv = reinterpret_cast<int32_t*>(L->tmp.img);
     a.g_bump = nullptr;
     a.s = s;
     a.collect_stats = L->opt.collect_stats > 0 ? 1 : 0;
@@ -282,11 +284,18 @@ int enqueue_event(psc_lattice* L, int s)
     const EventArgs a = event_args(L, s);
     const int threads = L->opt.block_threads;
     const int blocks = list_blocks(L, s);
+    // captured as a single-event graph: the event's last launch advances the
+    // device's event index to the next event
+    uint32_t* bump = L->capture_single ? &L->sc->g_base : nullptr;
+    const std::vector<int>& Q = L->reconcile[s];
+    // a list of at most a few hundred molecules: claim, commit and its own
+    // fill in one block, one launch
+    const bool one = L->general[s] && L->grid_class[s] <= 4;
     cudaEvent_t sp = span_open(L);
-    if (L->general[s] && L->grid_class[s] <= 4) {
-        // a list of at most a few hundred molecules: claim and commit in one
-        // block, one launch
-        launch_event_one(a, L->stream);
+    if (one) {
+        EventArgs a1 = a;
+        if (!L->fo2[s] && Q.size() == 1) a1.g_bump = bump;
+        launch_event_one(a1, L->stream);
         span_close(L, sp, kSpanClaim);
         L->launches += 1;
     } else {
@@ -303,15 +312,12 @@ int enqueue_event(psc_lattice* L, int s)
         L->table_used[cur ^ 1] = 0;
     }
     sp = (!L->reconcile[s].empty() || L->fo2[s]) ? span_open(L) : nullptr;
-    // captured as a single-event graph: the event's last launch advances the
-    // device's event index to the next event
-    uint32_t* bump = L->capture_single ? &L->sc->g_base : nullptr;
     // the due species' own list changes only through its own molecules, whose
     // commit noted the leavers; partner lists are checked against the grid,
-    // one after the other; then one launch fills every list, a block each
-    // (list order: the due species, then the partners; each list's scratch
-    // range follows those of the lists before it)
-    const std::vector<int>& Q = L->reconcile[s];
+    // one after the other; then one launch fills every list (but the own one
+    // of a one-block event), a block each (list order: the due species, then
+    // the partners; each list's scratch range follows those of the lists
+    // before it)
     uint32_t before = 0;
     for (int x : Q) {
         if (x != s) {
@@ -320,11 +326,15 @@ int enqueue_event(psc_lattice* L, int s)
         }
         before |= 1u << x;
     }
-    if (!Q.empty()) {
+    if (Q.size() > (one ? 1u : 0u)) {
         ListFill f{};
         f.r = reconcile_args(L, s);
         before = 0;
         for (size_t q = 0; q < Q.size(); ++q) {
+            if (one && Q[q] == s) {
+                before |= 1u << s;
+                continue;
+            }
             f.x[f.n] = Q[q];
             f.list[f.n] = L->model_h.lists[Q[q]];
             f.before[f.n] = before;

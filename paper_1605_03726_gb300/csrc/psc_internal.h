@@ -154,6 +154,8 @@ struct EventArgs {
     int32_t* leave;            // species with reactions: the commit notes here the slots of the due
                                // species' entries that react away (count in Scalars::tmp_count[s])
     uint32_t* g_bump;          // null, or the word the event's last launch sets to its index + 1
+    int32_t* holes;            // scratch of the own-list fill of a one-block event (the scratch
+    int32_t* surv;             // list's ids and img; img's decision bytes are read by then)
     int32_t s;                 // due species
     int32_t live;              // 1: the species writes its code into occ
     int32_t collect_stats;
@@ -259,8 +261,8 @@ struct ReconcileArgs {
 void upload_stencil(cudaStream_t st);
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
 void launch_commit(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st);
-// claim and commit of one event of a species with reactions in a single block
-// (lists of a few hundred molecules)
+// claim, commit and the own-list fill of one event of a species with
+// reactions in a single block (lists of a few hundred molecules)
 constexpr int kEventOneThreads = 512;
 void launch_event_one(const EventArgs& a, cudaStream_t st);
 void launch_fill_u64(uint64_t* p, uint64_t value, size_t n, int blocks, cudaStream_t st);

@@ -634,26 +634,6 @@ __global__ void __launch_bounds__(256) k_commit(const EventArgs a)
     commit_body<GENERAL, HASH>(a, event_index(a), blockIdx.x, gridDim.x);
 }
 
-// A whole event of a short list of a species with reactions in one block:
-// the claim phase, a block barrier (after which every claim of the event is
-// in place and visible to the block), the commit phase.  Claims the block
-// reads back and bits it tests change only through their winner, as across
-// launches.
-template <bool HASH>
-__global__ void __launch_bounds__(kEventOneThreads) k_event_one(const EventArgs a)
-{
-    const uint32_t g = event_index(a);
-    claim_body<true, HASH>(a, g, 0, 1);
-    __syncthreads();
-    commit_body<true, HASH>(a, g, 0, 1);
-}
-
-void launch_event_one(const EventArgs& a, cudaStream_t st)
-{
-    if (a.ct.hash) k_event_one<true><<<1, kEventOneThreads, 0, st>>>(a);
-    else k_event_one<false><<<1, kEventOneThreads, 0, st>>>(a);
-}
-
 void launch_claim(const EventArgs& a, bool general, int blocks, int threads, cudaStream_t st)
 {
     const bool hash = a.ct.hash != nullptr;
@@ -1057,10 +1037,47 @@ __global__ void __launch_bounds__(256) k_reconcile(const ReconcileArgs r, uint32
     reconcile_body(r, reconcile_event(r), blockIdx.x, gridDim.x, before);
 }
 
+// The fill of fill_body for the block whose threads (and atomics) wrote the
+// list's entries and counts in the same launch: counts and entries are read
+// through L2.
+__device__ __forceinline__ void fill_list(const SpeciesList& list, int32_t* count, int32_t k_left,
+                                          const int32_t* leave, int32_t* holes, int32_t* surv, int32_t* err)
+{
+    __shared__ int s_h, s_s;
+    const int32_t n = __ldcg(count);
+    const int32_t k = min(k_left, n);
+    if (k <= 0) return;
+    const int32_t n2 = n - k;
+    if (threadIdx.x == 0) {
+        s_h = 0;
+        s_s = 0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        const int32_t h = __ldcg(leave + q);
+        if (h < n2) holes[atomicAdd(&s_h, 1)] = h;
+    }
+    for (int p = n2 + threadIdx.x; p < n; p += blockDim.x)
+        if (__ldcg(list.vox + p) >= 0) surv[atomicAdd(&s_s, 1)] = p;
+    __syncthreads();
+    const int m = min(s_h, s_s);
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const int32_t h = holes[q], p = surv[q];
+        list.vox[h] = __ldcg(list.vox + p);
+        list.ids[h] = __ldcg(list.ids + p);
+        list.img[h] = __ldcg(list.img + p);
+    }
+    if (threadIdx.x == 0) {
+        *count = n2;
+        if (s_h != s_s) atomicOr(err, kErrListOverflow);
+    }
+}
+
 // One block per list: k entries left; the new length is n - k.  Every slot
 // below it that an entry left (a hole) takes one of the surviving entries at
 // or above it (there are as many); entries that left above it are simply cut
 // off.  The list's holes and survivors go to its range of the scratch arrays.
+// (fill_list does the same inside the launch that wrote the entries.)
 __device__ __forceinline__ void fill_body(const ReconcileArgs& r, uint32_t before)
 {
     __shared__ int s_h, s_s;
@@ -1116,6 +1133,30 @@ void launch_reconcile(const ReconcileArgs& r, uint32_t before, int blocks, int t
 void launch_fill(const ListFill& f, cudaStream_t st)
 {
     k_fill<<<f.n, 1024, 0, st>>>(f);
+}
+
+// A whole event of a short list of a species with reactions in one block:
+// the claim phase, a block barrier (after which every claim of the event is
+// in place and visible to the block), the commit phase, another barrier, and
+// the fill of the species' own list (its leavers' slots come first in the
+// scratch arrays).  Claims the block reads back and bits it tests change only
+// through their winner, as across launches.
+template <bool HASH>
+__global__ void __launch_bounds__(kEventOneThreads) k_event_one(const EventArgs a)
+{
+    const uint32_t g = event_index(a);
+    claim_body<true, HASH>(a, g, 0, 1);
+    __syncthreads();
+    commit_body<true, HASH>(a, g, 0, 1);
+    __syncthreads();
+    fill_list(a.list, &a.sc->counts[a.s], __ldcg(&a.sc->tmp_count[a.s]), a.leave, a.holes, a.surv, &a.sc->err);
+    if (threadIdx.x == 0 && a.g_bump) *a.g_bump = g + 1u;
+}
+
+void launch_event_one(const EventArgs& a, cudaStream_t st)
+{
+    if (a.ct.hash) k_event_one<true><<<1, kEventOneThreads, 0, st>>>(a);
+    else k_event_one<false><<<1, kEventOneThreads, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------

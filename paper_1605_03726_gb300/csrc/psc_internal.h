@@ -104,7 +104,7 @@ enum StatIndex {
 // Small device-resident scalars of one lattice.
 struct Scalars {
     int32_t counts[kMaxSpecies];     // molecules per species list
-    int32_t tmp_count[kMaxSpecies];  // survivors during a reconcile pass
+    int32_t tmp_count[kMaxSpecies];  // entries of each list that left in the current event
     uint32_t next_id;                // next fresh molecule id
     int32_t births;                  // births queued in the current event
     int32_t err;                     // kErr* bits

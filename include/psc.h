@@ -118,7 +118,9 @@ typedef struct {
 /* Tunables; zero in a field keeps the current value. */
 typedef struct {
     int32_t resort_period;    /* events of a species between Morton re-sorts of
-                                 its molecule list (default 64; <0 = never)     */
+                                 its molecule list (default 64; <0 = never);
+                                 lists holding fewer than 1/256 of the voxels
+                                 are not re-sorted (order never changes results) */
     int32_t block_threads;    /* threads per block of the event kernels (256)   */
     int32_t blocks_per_sm;    /* resident blocks per SM for grid sizing (8)     */
     int32_t collect_stats;    /* 1 = count attempts/hops/... (default 0), -1 off */

@@ -130,6 +130,15 @@ int32_t sort_limit(const psc_lattice* L, int x)
     return (int32_t)std::min<int64_t>(L->cap[x], 256 * (int64_t)L->grid_class[x]);
 }
 
+// Does Morton order pay for list x?  Only if the list holds at least 1/256 of
+// the voxels (by its estimate): sparser lists share too few cache lines
+// between neighbours in any order, and their re-sorts cost more than they
+// save.  A skipped re-sort changes no result.
+bool sorted_order_pays(const psc_lattice* L, int x)
+{
+    return !L->counts_h || L->est[x] * 256 >= L->V;
+}
+
 // Take the last background copy of the list lengths if it has landed, and
 // start the next one every 64 events.  The host queues events far faster than
 // the device runs them; once a copy is 256 events old the host waits for it,
@@ -357,10 +366,12 @@ int enqueue_event(psc_lattice* L, int s)
     L->events++;
     if (L->opt.resort_period > 0 && ++L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
         L->since_resort[s] = 0;
-        sp = span_open(L);
-        int rc = resort(L, s);
-        span_close(L, sp, kSpanResort);
-        if (rc) return rc;
+        if (sorted_order_pays(L, s)) {
+            sp = span_open(L);
+            int rc = resort(L, s);
+            span_close(L, sp, kSpanResort);
+            if (rc) return rc;
+        }
     }
     return cuda_fail(L, cudaPeekAtLastError());
 }
@@ -1245,8 +1256,12 @@ static int single_event(psc_lattice* L, int s, double t)
         finish();
         return rc;
     }
+    // the re-sort counter runs out after this event (1: the list is re-sorted,
+    // 2: its order does not pay, no re-sort)
     const uint8_t resort_now =
-        (L->opt.resort_period > 0 && L->since_resort[s] + 1 >= (uint64_t)L->opt.resort_period) ? 1 : 0;
+        (L->opt.resort_period > 0 && L->since_resort[s] + 1 >= (uint64_t)L->opt.resort_period)
+            ? (sorted_order_pays(L, s) ? 1 : 2)
+            : 0;
     std::vector<uint8_t> key;
     key.push_back((uint8_t)s);
     key.push_back((uint8_t)(L->g & 1u));
@@ -1553,10 +1568,12 @@ int drive(psc_lattice* L, double t_end, int64_t max_events)
             L->since_resort[s] += (uint64_t)e;
             if (L->opt.resort_period > 0 && L->since_resort[s] >= (uint64_t)L->opt.resort_period) {
                 L->since_resort[s] = 0;
-                cudaEvent_t sp = span_open(L);
-                rc = resort(L, s);
-                span_close(L, sp, kSpanResort);
-                if (rc) return rc;
+                if (sorted_order_pays(L, s)) {
+                    cudaEvent_t sp = span_open(L);
+                    rc = resort(L, s);
+                    span_close(L, sp, kSpanResort);
+                    if (rc) return rc;
+                }
             }
             continue;
         }

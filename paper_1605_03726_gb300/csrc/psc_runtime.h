@@ -181,6 +181,7 @@ void* dev_alloc(psc_lattice* L, size_t bytes);
 int event_blocks(const psc_lattice* L, int64_t work);
 int list_blocks(const psc_lattice* L, int x);
 int32_t sort_limit(const psc_lattice* L, int x);
+bool sorted_order_pays(const psc_lattice* L, int x);
 EventArgs event_args(const psc_lattice* L, int s);
 ReconcileArgs reconcile_args(const psc_lattice* L, int x);
 bool next_event(const psc_lattice* L, int* s_out, double* t_out);

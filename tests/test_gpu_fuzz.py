@@ -8,12 +8,19 @@ limits the library documents.  The whole state is compared with the oracle's
 synchronous rule every 60 events.  Together the seeds reach every branch of the
 event kernels' reaction paths: the due species' own list kept by its commit,
 partner lists reconciled, products appended, births, one-block events for
-short lists and the grid classes of growing and shrinking lists.
+short lists and the grid classes of growing and shrinking lists.  A second
+set adds compartments (slabs, a round cell or voxel noise; Sec. 2) and FCC
+lattices, and checks that the library accepts and refuses every step of the
+model exactly as the oracle does.
 """
 import random
 
+import numpy as np
 import pytest
 
+import models
+import oracle
+import paper_1605_03726_gb300 as psc
 from test_gpu_parity import assert_same, build_both
 
 pytestmark = pytest.mark.gpu
@@ -63,3 +70,88 @@ def test_random_reaction_models(seed):
         g.run_events(60)
         o.run_events(60)
         assert_same(g, o, "seed %d (%d reactions) after %d events" % (seed, n_rx, 60 * (step + 1)))
+
+
+def _outcome(fn, *args, **kw):
+    """(return value, None) or (None, status code of the refusal)"""
+    try:
+        return fn(*args, **kw), None
+    except (psc.EngineError, oracle.OracleError) as e:
+        return None, e.rc
+
+
+def random_compartment_model(seed):
+    """Ops of a seeded model with compartments (slabs, a round cell or voxel
+    noise), species placed in them and random reactions, on an HCP or FCC
+    lattice; the library must accept and refuse exactly what the oracle does."""
+    rnd = random.Random(10_000 + seed)
+    shape = (rnd.choice([16, 20, 24]), rnd.choice([16, 18, 24]), rnd.choice([12, 18, 24]))
+    ni, nj, nk = shape
+    V = ni * nj * nk
+    flags = rnd.randrange(8) | (oracle.FCC if rnd.random() < 0.3 else 0)
+    kind = rnd.choice(["slabs", "cell", "noise"])
+    if kind == "slabs":
+        nc = rnd.randint(2, 3)
+        axis = rnd.randrange(3)
+        idx = np.indices((nk, nj, ni))[2 - axis].reshape(-1)
+        lab = (idx * nc // shape[axis]).astype(np.uint8)
+    elif kind == "cell":
+        nc = 3
+        lab = models.cell_labels(ni, nj, nk, radius=rnd.uniform(8.0, 14.0))
+    else:
+        nc = rnd.randint(2, 4)
+        lab = np.random.default_rng(seed).integers(0, nc, V).astype(np.uint8)
+    ns = rnd.randint(2, 5)
+    species = [(0.0 if (s > 0 and rnd.random() < 0.2) else rnd.choice([0.5e-12, 1e-12, 3e-12]),
+                int(V * rnd.uniform(0.0, 0.05)), rnd.randrange(nc)) for s in range(ns)]
+    comp = [c for _, _, c in species]
+
+    def in_comp(c):
+        # a species of compartment c, or any species when none is there (the
+        # model may then be refused, as it must be on both sides)
+        pool = [s for s in range(ns) if comp[s] == c]
+        return rnd.choice(pool) if pool and rnd.random() < 0.8 else rnd.randrange(ns)
+
+    reactions = []
+    for _ in range(rnd.randint(1, 6)):
+        npr = rnd.choice([0, 1, 1, 2])
+        if rnd.random() < 0.4:
+            r = [rnd.randrange(ns)]
+            k = rnd.uniform(50.0, 1500.0)
+            prods = [in_comp(comp[r[0]]) for _ in range(npr)]
+        else:
+            r = rnd.sample(range(ns), 2)
+            k = 10.0 ** rnd.uniform(-20.5, -18.5)
+            prods = [in_comp(comp[r[1]]), in_comp(comp[r[0]])][:npr]
+        reactions.append((r, prods, k))
+    return shape, flags, lab, nc, species, reactions
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_random_models_with_compartments(seed):
+    shape, flags, lab, nc, species, reactions = random_compartment_model(seed)
+    (g, eg), (o, eo) = (_outcome(psc.Lattice, *shape, voxel_radius=1e-8, boundary=flags),
+                        _outcome(oracle.Lattice, *shape, 1e-8, flags, oracle.RULE_SYNC))
+    assert eg == eo, (seed, eg, eo)
+    if eg is not None:
+        return                                   # both refuse the lattice (e.g. periodic FCC k)
+    assert _outcome(g.set_compartments, lab, nc)[1] == _outcome(o.set_compartments, lab, nc)[1]
+    for D, n, c in species:
+        sg, sg_err = _outcome(g.add_species, D, n, compartment=c)
+        so, so_err = _outcome(o.add_species, D, n)
+        if so_err is None:
+            so_err = _outcome(o.species_compartment, so, c)[1]
+        assert sg_err == so_err, (seed, sg_err, so_err)
+    for r, p, k in reactions:
+        assert _outcome(g.add_reaction, r, p, k)[1] == _outcome(o.add_reaction, r, p, k)[1], (seed, r, p)
+    rg, eg = _outcome(g.populate, 200 + seed)
+    ro, eo = _outcome(o.populate, 200 + seed)
+    assert (rg, eg) == (ro, eo), seed
+    if eg is None:
+        assert_same(g, o, "seed %d populate" % seed)
+        for step in range(3):
+            g.run_events(50)
+            o.run_events(50)
+            assert_same(g, o, "seed %d after %d events" % (seed, 50 * (step + 1)))
+    g.close()
+    o.close()

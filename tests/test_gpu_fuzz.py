@@ -11,7 +11,9 @@ partner lists reconciled, products appended, births, one-block events for
 short lists and the grid classes of growing and shrinking lists.  A second
 set adds compartments (slabs, a round cell or voxel noise; Sec. 2) and FCC
 lattices, and checks that the library accepts and refuses every step of the
-model exactly as the oracle does.
+model exactly as the oracle does.  A third set runs diffusion workloads (whole
+or partial bricks, walls, crowders, several walkers, a drawn box count) on
+both owner-computes tile kernels.
 """
 import random
 
@@ -155,3 +157,37 @@ def test_random_models_with_compartments(seed):
             assert_same(g, o, "seed %d after %d events" % (seed, 50 * (step + 1)))
     g.close()
     o.close()
+
+
+def random_tile_case(seed):
+    """A seeded diffusion workload for the owner-computes tile kernels: shape
+    (whole or partial bricks), walls, occupancy, crowders and box count."""
+    rnd = random.Random(20_000 + seed)
+    ni = rnd.choice([24, 32, 40, 48, 64, 30, 38])
+    nj = rnd.choice([16, 24, 32, 40, 22, 34])
+    nk = rnd.choice([12, 16, 20, 24, 30, 40])
+    walls = rnd.randrange(8)
+    V = ni * nj * nk
+    crowd = rnd.choice([0.0, 0.0, 0.1, 0.3])
+    walkers = [(rnd.choice([1e-12, 2e-12, 5e-12]), int(V * rnd.uniform(0.005, 0.15)))
+               for _ in range(rnd.randint(1, 2))]
+    regions = rnd.choice([0, 0, 4, 8, 12, 16, 27])
+
+    def recipe(L):
+        if crowd:
+            L.add_species(0.0, int(crowd * V))
+        for D, n in walkers:
+            L.add_species(D, n)
+
+    return (ni, nj, nk), walls, recipe, regions
+
+
+@pytest.mark.parametrize("lean", [1, -1])
+@pytest.mark.parametrize("seed", range(24))
+def test_random_tile_kernel_workloads(seed, lean):
+    shape, walls, recipe, regions = random_tile_case(seed)
+    g, o = build_both(shape, recipe, 300 + seed, boundary=walls, tiles=1, tile_regions=regions, tile_lean=lean)
+    for chunk in (1, 9, 30):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, "seed %d lean %d after chunk %d" % (seed, lean, chunk))

@@ -13,7 +13,8 @@ set adds compartments (slabs, a round cell or voxel noise; Sec. 2) and FCC
 lattices, and checks that the library accepts and refuses every step of the
 model exactly as the oracle does.  A third set runs diffusion workloads (whole
 or partial bricks, walls, crowders, several walkers, a drawn box count) on
-both owner-computes tile kernels.
+both owner-computes tile kernels, and a fourth the same kind of workloads
+under the sub-volume rule (Sec. 2.5) against the oracle's sub-volume mode.
 """
 import random
 
@@ -191,3 +192,43 @@ def test_random_tile_kernel_workloads(seed, lean):
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, "seed %d lean %d after chunk %d" % (seed, lean, chunk))
+
+
+def random_subvolume_case(seed):
+    """A seeded workload for the sub-volume rule: shape (periodic axes a
+    multiple of 4), walls, immobile crowders and one to three walker species
+    with different hop intervals."""
+    rnd = random.Random(30_000 + seed)
+    walls = rnd.randrange(8)
+    dims = []
+    for a in range(3):
+        choices = [16, 20, 24, 32] if walls & (1 << a) else [14, 18, 22, 26, 30]
+        dims.append(rnd.choice(choices))
+    V = dims[0] * dims[1] * dims[2]
+    crowd = rnd.choice([0.0, 0.15, 0.3])
+    walkers = [(rnd.choice([0.5e-12, 1e-12, 4e-12]), int(V * rnd.uniform(0.01, 0.2)))
+               for _ in range(rnd.randint(1, 3))]
+
+    def recipe(L):
+        if crowd:
+            L.add_species(0.0, int(crowd * V))
+        for D, n in walkers:
+            L.add_species(D, n)
+
+    return tuple(dims), walls, recipe
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_subvolume_workloads(seed):
+    shape, walls, recipe = random_subvolume_case(seed)
+    g = psc.Lattice(*shape, voxel_radius=1e-8, boundary=walls)
+    g.set_options(subvolume=1)
+    o = oracle.Lattice(*shape, 1e-8, walls, oracle.RULE_SUBVOL)
+    recipe(g)
+    recipe(o)
+    assert g.populate(400 + seed) == o.populate(400 + seed)
+    assert_same(g, o, "populate")
+    for chunk in (1, 9, 30):
+        g.run_events(chunk)
+        o.run_events(chunk)
+        assert_same(g, o, "seed %d after chunk %d" % (seed, chunk))

@@ -14,7 +14,8 @@ lattices, and checks that the library accepts and refuses every step of the
 model exactly as the oracle does.  A third set runs diffusion workloads (whole
 or partial bricks, walls, crowders, several walkers, a drawn box count) on
 both owner-computes tile kernels, and a fourth the same kind of workloads
-under the sub-volume rule (Sec. 2.5) against the oracle's sub-volume mode.
+under the sub-volume rule (Sec. 2.5) against the oracle's sub-volume mode;
+and the first set's models also run as members of one batch.
 """
 import random
 
@@ -232,3 +233,30 @@ def test_random_subvolume_workloads(seed):
         g.run_events(chunk)
         o.run_events(chunk)
         assert_same(g, o, "seed %d after chunk %d" % (seed, chunk))
+
+
+def test_random_reaction_models_in_one_batch():
+    """The randomised reaction models of the first set as members of one batch
+    (one launch per event phase over all members), each bit-exact with the
+    oracle at every checkpoint."""
+    import torch
+    stream = torch.cuda.Stream()
+    B = psc.Batch(stream=stream.cuda_stream)
+    pairs = []
+    for seed in range(24):
+        shape, walls, recipe, _ = random_model(seed)
+        g = psc.Lattice(*shape, voxel_radius=1e-8, boundary=walls, stream=stream.cuda_stream)
+        g.set_options(claim_table=1)
+        o = oracle.Lattice(*shape, 1e-8, walls, oracle.RULE_SYNC)
+        recipe(g)
+        recipe(o)
+        assert g.populate(100 + seed) == o.populate(100 + seed)
+        B.add(g)
+        pairs.append((seed, g, o))
+    for chunk in (20, 40, 60):
+        B.run_events(chunk)
+        torch.cuda.synchronize()
+        for seed, g, o in pairs:
+            o.run_events(chunk)
+            assert_same(g, o, "batch member %d after chunk %d" % (seed, chunk))
+    B.close()

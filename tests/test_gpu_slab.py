@@ -6,7 +6,8 @@ refreshed boundary layers.  Several slabs held by one process exchange by
 device copies; the results must equal the oracle's synchronous rule on the
 whole lattice bit for bit: every molecule's position, id and unwrapped
 position.  Also: one slab on a periodic axis (its own neighbour), caller-owned
-exchange buffers driven through the per-rank protocol, and the refusals.
+exchange buffers driven through the per-rank protocol, the refusals, and
+randomised splits (shapes, walls, slab counts, crowders, occupancy).
 """
 import numpy as np
 import pytest
@@ -155,5 +156,43 @@ def test_slabs_at_full_size_match_the_whole_lattice():
     lu, _ = L.unwrapped(s)
     assert np.array_equal(ids, lid) and np.array_equal(ijk, li) and np.array_equal(xyz, lu)
     for sl in slabs:
+        sl.close()
+    L.close()
+
+
+def _random_slab_case(seed):
+    """A seeded slab workload: shape (nk a multiple of the slab count, every
+    slab at least two layers thick), walls, crowders, occupancy, slab count."""
+    import random
+    rnd = random.Random(40_000 + seed)
+    count = rnd.randint(1, 6)
+    m = rnd.randint(2, 8)
+    nk = count * m
+    if nk % 2:
+        nk += count                          # nk even: one more layer per slab
+    walls = rnd.randrange(8)
+    if walls & psc.PERIODIC_K and nk < 4:
+        walls &= ~psc.PERIODIC_K
+    shape = (rnd.choice([16, 20, 24, 30, 40]), rnd.choice([12, 16, 20, 28]), nk)
+    return shape, walls, count, rnd.choice([0.0, 0.1, 0.3]), rnd.uniform(0.01, 0.4)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_slab_splits_match_oracle(seed):
+    shape, boundary, count, crowd, frac = _random_slab_case(seed)
+    V = shape[0] * shape[1] * shape[2]
+    L = psc.Lattice(*shape, voxel_radius=1e-8, boundary=boundary)
+    o = oracle.Lattice(*shape, 1e-8, boundary, oracle.RULE_SYNC)
+    s = _models(L, V, crowd, frac)
+    _models(o, V, crowd, frac)
+    L.populate(50 + seed)
+    o.populate(50 + seed)
+    slabs = [psc.Slab(L, s, q, count) for q in range(count)]
+    for chunk in (1, 9, 30):
+        psc.run_slabs(slabs, chunk)
+        o.run_events(chunk)
+        _same(slabs, o, s, "seed %d chunk %d" % (seed, chunk))
+    for sl in slabs:
+        sl.synchronize()
         sl.close()
     L.close()

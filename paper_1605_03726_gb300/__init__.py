@@ -306,16 +306,16 @@ class Lattice:
     def coords(self, species):
         n = ctypes.c_int64()
         _check("psc_coords", lib().psc_coords(self._h, species, None, None, 0, ctypes.byref(n)), (OK, E_ARG))
-        ijk = np.zeros((max(1, n.value), 3), dtype=np.int32)
-        ids = np.zeros(max(1, n.value), dtype=np.uint32)
+        ijk = np.empty((max(1, n.value), 3), dtype=np.int32)     # every entry is written
+        ids = np.empty(max(1, n.value), dtype=np.uint32)
         _check("psc_coords", lib().psc_coords(self._h, species, _ptr(ijk), _ptr(ids), n.value, ctypes.byref(n)))
         return ijk[: n.value], ids[: n.value]
 
     def unwrapped(self, species):
         n = ctypes.c_int64()
         _check("psc_unwrapped", lib().psc_unwrapped(self._h, species, None, None, 0, ctypes.byref(n)), (OK, E_ARG))
-        xyz = np.zeros((max(1, n.value), 3), dtype=np.int32)
-        ids = np.zeros(max(1, n.value), dtype=np.uint32)
+        xyz = np.empty((max(1, n.value), 3), dtype=np.int32)     # every entry is written
+        ids = np.empty(max(1, n.value), dtype=np.uint32)
         _check("psc_unwrapped", lib().psc_unwrapped(self._h, species, _ptr(xyz), _ptr(ids), n.value,
                                                     ctypes.byref(n)))
         return xyz[: n.value], ids[: n.value]

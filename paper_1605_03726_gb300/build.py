@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsc.so")
-SOURCES = ["psc_kernels.cu", "psc_sort.cu", "psc_api.cpp", "psc_batch.cpp", "psc_tune.cpp", "psc_static.cu", "psc_slab.cpp"]
-HEADERS = [os.path.join(CSRC, "psc_internal.h"), os.path.join(CSRC, "psc_runtime.h"), os.path.join(CSRC, "psc_tiles.cuh"), os.path.join(CSRC, "psc_tiles_lean.cuh"), os.path.join(CSRC, "psc_slab.cuh"), os.path.join(CSRC, "psc_subvol.cuh"), os.path.join(ROOT, "include", "psc.h")]
+SOURCES = ["psc_kernels.cu", "psc_sort.cu", "psc_api.cpp", "psc_batch.cpp", "psc_tune.cpp", "psc_static.cu", "psc_slab.cpp",
+           "psc_readout.cu"]
+HEADERS = [os.path.join(CSRC, "psc_internal.h"), os.path.join(CSRC, "psc_runtime.h"), os.path.join(CSRC, "psc_tiles.cuh"), os.path.join(CSRC, "psc_tiles_lean.cuh"), os.path.join(CSRC, "psc_slab.cuh"), os.path.join(CSRC, "psc_subvol.cuh"), os.path.join(CSRC, "psc_readout.h"), os.path.join(ROOT, "include", "psc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O3",
                 "-Xptxas", "-O3", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -8,6 +8,7 @@
 // from device memory, so the host never waits for the device between events.
 #include "psc.h"
 #include "psc_internal.h"
+#include "psc_readout.h"
 #include "psc_runtime.h"
 
 #include <algorithm>
@@ -1696,15 +1697,49 @@ static void order_by_id(const std::vector<uint32_t>& ids, std::vector<int64_t>& 
     std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return ids[x] < ids[y]; });
 }
 
+// The n molecules of list s in id order, built on the device (ids sorted with
+// their slots, then one gather) and copied to the caller's host buffers in
+// one piece each.  Used when the list fits the re-sort scratch; returns
+// PSC_OK, an error, or 1 when the caller should build the answer on the host.
+static int device_positions(psc_lattice* L, int32_t s, int64_t n, bool unwrapped, int32_t* out,
+                            uint32_t* ids_out)
+{
+    if (n <= 0 || n > L->rs_max) return 1;
+    if (n > L->readout_cap) {
+        if (L->readout) dev_free_one(L, L->readout);
+        L->readout = (int32_t*)dev_alloc(L, (size_t)n * 16);
+        L->readout_cap = L->readout ? n : 0;
+        if (!L->readout) return 1;
+    }
+    int32_t* pos = L->readout;
+    uint32_t* ids = reinterpret_cast<uint32_t*>(L->readout + 3 * n);
+    const int blocks = event_blocks(L, n);
+    if (readout_positions(L->model_h.lists[s], (int32_t)n, L->ni, L->nj, L->nk, unwrapped,
+                          (L->bflags & PSC_FCC) != 0, L->rs_keys, L->rs_vals, L->rs_scratch, pos, ids, blocks,
+                          L->stream, &L->launches) != 0)
+        return cuda_fail(L, cudaErrorUnknown);
+    int rc = cuda_fail(L, cudaMemcpyAsync(out, pos, (size_t)n * 12, cudaMemcpyDeviceToHost, L->stream));
+    if (!rc && ids_out)
+        rc = cuda_fail(L, cudaMemcpyAsync(ids_out, ids, (size_t)n * 4, cudaMemcpyDeviceToHost, L->stream));
+    if (!rc) rc = cuda_fail(L, cudaStreamSynchronize(L->stream));
+    if (rc) return rc;
+    L->d2h += (uint64_t)n * (ids_out ? 16 : 12);
+    return PSC_OK;
+}
+
 int psc_coords(psc_lattice* L, int32_t s, int32_t* ijk, uint32_t* ids_out, int64_t cap, int64_t* n_out)
 {
     if (!L || !n_out || s < 0 || s >= L->nsp) return PSC_E_ARG;
     if (!L->populated) return PSC_E_ORDER;
     DevGuard dg(L->device);
     if (!ijk || cap <= 0) return list_size(L, s, n_out);
+    int rc = list_size(L, s, n_out);               // E_ARG here only says the list is not empty
+    if (rc != PSC_OK && rc != PSC_E_ARG) return rc;
+    if (*n_out > cap) return PSC_E_ARG;
+    if ((rc = device_positions(L, s, *n_out, false, ijk, ids_out)) <= 0) return rc;
     std::vector<int32_t> vox;
     std::vector<uint32_t> ids;
-    int rc = read_list(L, s, vox, ids, nullptr);
+    rc = read_list(L, s, vox, ids, nullptr);
     if (rc) return rc;
     const int64_t n = (int64_t)vox.size();
     *n_out = n;
@@ -1728,10 +1763,14 @@ int psc_unwrapped(psc_lattice* L, int32_t s, int32_t* xyz, uint32_t* ids_out, in
     if (!L->populated) return PSC_E_ORDER;
     DevGuard dg(L->device);
     if (!xyz || cap <= 0) return list_size(L, s, n_out);
+    int rc = list_size(L, s, n_out);               // E_ARG here only says the list is not empty
+    if (rc != PSC_OK && rc != PSC_E_ARG) return rc;
+    if (*n_out > cap) return PSC_E_ARG;
+    if ((rc = device_positions(L, s, *n_out, true, xyz, ids_out)) <= 0) return rc;
     std::vector<int32_t> vox;
     std::vector<uint32_t> ids;
     std::vector<uint64_t> img;
-    int rc = read_list(L, s, vox, ids, &img);
+    rc = read_list(L, s, vox, ids, &img);
     if (rc) return rc;
     const int64_t n = (int64_t)vox.size();
     *n_out = n;
@@ -1929,6 +1968,7 @@ int psc_device_bytes(const psc_lattice* L, int64_t* bytes)
     const auto& T = L->tile;
     b += T.slots * 4 * 5 + (int64_t)T.regions * 4 * 4 + T.ids * 8 + T.halo_entries * (int64_t)sizeof(uint2);
     if (T.claim) b += L->V * 4;
+    b += L->readout_cap * 16;                        // staging of the device-side read-out, once used
     *bytes = b;
     return PSC_OK;
 }

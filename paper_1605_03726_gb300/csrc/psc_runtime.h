@@ -81,6 +81,8 @@ struct psc_lattice {
     uint32_t* rs_vals = nullptr;
     SortScratch rs_scratch;
     int64_t rs_max = 0;
+    int32_t* readout = nullptr;          // staging of the device-side read-out (16 bytes per molecule)
+    int64_t readout_cap = 0;
 
     bool general[kMaxSpecies] = {};
     // automatic stretch kernel (psc_options.tiles = 0) of species with a tile

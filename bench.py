@@ -570,6 +570,18 @@ def reaction_workloads(args):
     ]
 
 
+def selected_workloads(args):
+    """The reaction workloads --configs names (all three when it names none);
+    an unknown name is an error."""
+    ws = reaction_workloads(args)
+    wanted = [x for x in args.configs.split(",") if x]
+    unknown = sorted(set(wanted) - {w["name"] for w in ws})
+    if unknown:
+        raise SystemExit("bench.py: unknown reaction workload(s) %s; known: %s"
+                         % (", ".join(unknown), ", ".join(w["name"] for w in ws)))
+    return [w for w in ws if not wanted or w["name"] in wanted]
+
+
 def _reaction_gpu(psc, torch, w, local, stats):
     stream = torch.cuda.Stream(device=local)
     L = psc.Lattice(*w["shape"], voxel_radius=RV, boundary=w["boundary"], device=local, stream=stream.cuda_stream)
@@ -626,10 +638,7 @@ def reaction_arm(args, local):
     import paper_1605_03726_gb300 as psc
     hbm, peak_kind = peaks()
     out = {}
-    wanted = set(x for x in args.configs.split(",") if x)
-    for w in reaction_workloads(args):
-        if wanted and w["name"] not in wanted:
-            continue
+    for w in selected_workloads(args):
         _reaction_gpu(psc, torch, w, local, False)                # warm-up (allocations, graphs)
         run = _reaction_gpu(psc, torch, w, local, False)
         cnt = _reaction_gpu(psc, torch, w, local, True)

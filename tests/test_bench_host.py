@@ -51,3 +51,22 @@ def test_serving_cpu_baseline_on_two_cores():
     assert out["cores"] == 2 and out["kind"] == "oracle" and out["unit"] == "replicas/s"
     assert "6 ended" in out["sample"]                             # small replicas all end in time
     assert out["value"] > 0 and out["attempts_per_s"] > 0
+
+
+def _args(*argv):
+    old = sys.argv
+    sys.argv = ["bench.py"] + list(argv)
+    try:
+        return bench.parse()
+    finally:
+        sys.argv = old
+
+
+def test_reaction_workloads_are_selected_by_name():
+    names = [w["name"] for w in bench.selected_workloads(_args())]
+    assert names == ["ab_64cubed", "crowded_256cubed", "mapk_200cubed"]
+    picked = bench.selected_workloads(_args("--configs", "mapk_200cubed,ab_64cubed", "--config-events", "50"))
+    assert [w["name"] for w in picked] == ["ab_64cubed", "mapk_200cubed"]
+    assert picked[1]["events"] == 50
+    with pytest.raises(SystemExit):
+        bench.selected_workloads(_args("--configs", "crowded"))
